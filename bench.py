@@ -1,0 +1,412 @@
+"""Benchmark of the hypercube-queue stationary solver on one GB300 (or N replicas).
+
+Workload (default): N=24 units, J=1000 clustered demand nodes, infinite queue,
+nu log-uniform on [1,3], load 0.8 -- 2^24 = 16.8M states.  One step = load the
+instance from device memory (validation + upward-rate table build), solve to a
+relative global-balance residual of 1e-10 (FP32 sweeps, then DF64 sweeps; FP64
+scalars and residual), and write P, rho, R, W to device memory.
+
+Metric: state-updates/s = (2^N - 2) x sweeps / time, whole job.  Reported beside it:
+time-to-1e-10-residual of the plain FP64 iteration and of the other precision
+paths on the same instance and GPU, the DF64 sweep's HBM roofline, and the CPU
+oracle timed on a bounded sample of the same workload.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun every rank solves its own instance of the same shape (replicas;
+the method has no cross-GPU exchange in this configuration).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2603_03019_gb300 import instances as I  # noqa: E402
+
+WORKLOADS = {
+    "n24": lambda seed: I.large_infinite_n24(seed),
+    "n23": lambda seed: I.large_infinite_n24(seed, N=23),
+    "n20": lambda seed: I.mixed_n20(seed, 0.6),
+    "n10": lambda seed: I.small_loss_n10(seed),
+}
+BASE_SEED = {"n24": 3001, "n23": 3001, "n20": 2001, "n10": 1001}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="n24", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default="fp32+df64")
+    ap.add_argument("--tol", type=float, default=1e-10)
+    ap.add_argument("--no-compare", action="store_true", help="skip the per-precision comparison")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--profile", action="store_true",
+                    help="one instance load and `--sweeps` DF64 sweeps, nothing else (for ncu)")
+    ap.add_argument("--sweeps", type=int, default=2)
+    return ap.parse_args()
+
+
+def run_profile(args):
+    """The smallest run that contains every kernel of the hot path once per layer."""
+    import torch
+
+    from paper_2603_03019_gb300 import hq
+
+    inst = WORKLOADS[args.workload](BASE_SEED[args.workload])
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(device=dev)
+    s = hq.Solver(inst.N, inst.J, inst.mode, inst.C, stream=stream)
+    s.load(torch.tensor(inst.lam_j, device=dev), torch.tensor(inst.nu, device=dev),
+           torch.tensor(inst.pref, device=dev))
+    torch.cuda.synchronize()
+    rc, st = s.solve(tol=0.0, tol_kind=hq.HQ_TOL_STEP, precision="df64", max_sweeps=args.sweeps,
+                     check_every=args.sweeps)
+    s.close()
+    print(json.dumps({"profile": inst.name, "sweeps": st["sweeps_hi"], "rc": rc}))
+    return 0
+
+
+def dist_info():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(tempfile.gettempdir(), f"hq_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                t = [x.strip() for x in line.split(",")]
+                if len(t) < 9:
+                    continue
+                try:
+                    sm.append(float(t[1]))
+                    smax.append(float(t[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, t[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def cpu_oracle_sample(inst, layer: int | None = None) -> dict:
+    """Algorithm 1's update of one whole layer (literal inner loop) by the CPU oracle,
+    on the same instance: the dispatch rows of the layer below are built first (not
+    timed, as the paper times coefficient generation separately)."""
+    import oracle
+
+    N = inst.N
+    n = N // 2 if layer is None else layer
+    o = oracle.Oracle(inst)
+    t0 = time.perf_counter()
+    o.build_table(n - 1, n - 1)
+    t_table = time.perf_counter() - t0
+    o.init()
+    t0 = time.perf_counter()
+    r, md, l1 = o.update_layer(n)
+    t = time.perf_counter() - t0
+    states = math.comb(N, n)
+    o.close()
+    return {"value": states / t, "unit": "state-updates/s", "cores": 1, "kind": "oracle",
+            "sample": f"one Algorithm-1 update of layer {n} ({states} states, {r} inner "
+                      f"iterations) of the same N={N} instance; its dispatch rows built "
+                      f"first in {t_table:.1f} s (not timed)",
+            "seconds": t}
+
+
+def run_reference(args):
+    ws, rank, local = dist_info()
+    if rank != 0:
+        return 0
+    inst = WORKLOADS[args.workload](BASE_SEED[args.workload])
+    import oracle
+
+    N = inst.N
+    n = N // 2
+    o = oracle.Oracle(inst)
+    o.build_table(n - 1, n - 1)
+    o.init()
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        r, md, l1 = o.update_layer(n)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+        o.init()
+    o.close()
+    states = math.comb(N, n)
+    total = sum(times)
+    value = states * len(times) / total
+    line = {"metric": "state-updates/s (Algorithm 1, CPU oracle)", "value": value,
+            "unit": "state-updates/s", "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000 * total / len(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": inst.name, "N": N, "J": inst.J, "mode": "infinite",
+                       "sample": f"layer {n} update per step"},
+            "cpu_baseline": {"value": value, "unit": "state-updates/s", "cores": 1,
+                             "kind": "oracle",
+                             "sample": f"one Algorithm-1 update of layer {n} ({states} states) "
+                                       f"per step, same instance"},
+            "e2e": {"value": value, "unit": "state-updates/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    import torch
+
+    from paper_2603_03019_gb300 import hq
+
+    ws, rank, local = dist_info()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+    hq.load()
+    stream = torch.cuda.Stream(device=dev)
+    inst = WORKLOADS[args.workload](BASE_SEED[args.workload] + 97 * rank)
+    N, J = inst.N, inst.J
+    lam_d = torch.tensor(inst.lam_j, device=dev)
+    nu_d = torch.tensor(inst.nu, device=dev)
+    pref_d = torch.tensor(inst.pref, device=dev)
+    S = 1 << N
+    out_P = torch.empty(S, dtype=torch.float64, device=dev)
+    out_rho = torch.empty(N, dtype=torch.float64, device=dev)
+    out_R = torch.empty(J * N, dtype=torch.float64, device=dev)
+    out_W = torch.empty(N * J, dtype=torch.float64, device=dev)
+    solver = hq.Solver(N, J, inst.mode, inst.C, stream=stream)
+    prec = hq.PRECISION[args.precision]
+
+    def opts(precision=prec, tol=args.tol):
+        o = hq.hq_default_opts()
+        o.tol = tol
+        o.tol_kind = hq.HQ_TOL_RESIDUAL
+        o.precision = precision
+        o.check_every = 8
+        return o
+
+    def step_device():
+        hq.hq_load(solver.h, lam_d, nu_d, pref_d)
+        rc, st = hq.hq_solve(solver.h, opts())
+        hq.hq_get_stationary(solver.h, out_P)
+        hq.hq_get_utilisation(solver.h, out_rho)
+        hq.hq_get_response_pattern(solver.h, out_R)
+        hq.hq_get_workload(solver.h, out_W)
+        return rc, st
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+
+            dist.barrier()
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step_device()
+        torch.cuda.synchronize()
+        barrier()
+        clocks = ClockSampler(local)
+        clocks.start()
+        hq.hq_launch_count(reset=True)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        sweeps_total, stats = 0, []
+        for _ in range(args.steps):
+            rc, st = step_device()
+            stats.append(st.as_dict())
+            sweeps_total += st.sweeps_fp32 + st.sweeps_hi
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        launches = hq.hq_launch_count()
+        clk = clocks.stop()
+        barrier()
+        ms = ev0.elapsed_time(ev1)
+        if ws > 1:
+            import torch.distributed as dist
+
+            t = torch.tensor([ms, float(sweeps_total)], dtype=torch.float64, device=dev)
+            tm = t.clone()
+            dist.all_reduce(tm[:1], op=dist.ReduceOp.MAX)
+            dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
+            ms, sweeps_all = float(tm[0]), float(t[1])
+        else:
+            sweeps_all = float(sweeps_total)
+        value = (S - 2) * sweeps_all / (ms / 1000.0)
+
+        # ---- end to end through the public API with host buffers --------------------------
+        e2e = None
+        if not args.no_e2e:
+            lam_h = torch.tensor(inst.lam_j).pin_memory()
+            nu_h = torch.tensor(inst.nu).pin_memory()
+            pref_h = torch.tensor(inst.pref).pin_memory()
+            P_h = torch.empty(S, dtype=torch.float64).pin_memory()
+            rho_h = torch.empty(N, dtype=torch.float64).pin_memory()
+            R_h = torch.empty(J * N, dtype=torch.float64).pin_memory()
+            W_h = torch.empty(N * J, dtype=torch.float64).pin_memory()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            sw = 0
+            for _ in range(args.steps):
+                hq.hq_load(solver.h, lam_h, nu_h, pref_h)
+                rc, st = hq.hq_solve(solver.h, opts())
+                hq.hq_get_stationary(solver.h, P_h)
+                hq.hq_get_utilisation(solver.h, rho_h)
+                hq.hq_get_response_pattern(solver.h, R_h)
+                hq.hq_get_workload(solver.h, W_h)
+                sw += st.sweeps_fp32 + st.sweeps_hi
+            torch.cuda.synchronize()
+            te = time.perf_counter() - t0
+            h2d = inst.lam_j.nbytes + inst.nu.nbytes + inst.pref.nbytes
+            d2h = (S + N + 2 * J * N) * 8
+            e2e = {"value": (S - 2) * sw * ws / te, "unit": "state-updates/s",
+                   "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                   "ms_per_step": 1000 * te / args.steps}
+
+        # ---- time to tolerance per precision path (same instance, same GPU) -------------------
+        compare = {}
+        if not args.no_compare and rank == 0:
+            hq.hq_load(solver.h, lam_d, nu_d, pref_d)
+            for name in ("fp64", "df64", "fp32+df64"):
+                rc, st = hq.hq_solve(solver.h, opts(hq.PRECISION[name]))
+                compare[name] = {"ms": round(st.ms_total, 3), "sweeps_fp32": st.sweeps_fp32,
+                                 "sweeps_hi": st.sweeps_hi, "residual": st.final_residual,
+                                 "converged": bool(st.converged)}
+            if "fp64" in compare and compare["fp64"]["ms"] > 0:
+                for name in compare:
+                    compare[name]["speedup_vs_fp64"] = round(compare["fp64"]["ms"] / compare[name]["ms"], 3)
+
+        # ---- roofline of the DF64 sweep (the kernels that dominate the step) ------------------
+        roof = None
+        if rank == 0:
+            hq.hq_load(solver.h, lam_d, nu_d, pref_d)
+            hq.hq_solve(solver.h, opts())
+            kms = hq.hq_profile_sweep(solver.h, hq.HQ_PREC_DF64, 5, N)
+            sweep_ms = float(kms.sum())
+            gather_ms = float(kms[0::2].sum())
+            nbytes = hq.hq_sweep_bytes(solver.h, hq.HQ_PREC_DF64)
+            peak, kind = measured_peaks()
+            ach = nbytes / (sweep_ms / 1000.0) / 1e9
+            big = int(np.argmax(kms[0::2]))
+            roof = {"bound": "hbm", "kernel": "DF64 sweep: k_gather<PolDF> + k_update<PolDF>, "
+                    "layers 1..N-1 (one outer iteration)", "achieved": round(ach, 1),
+                    "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4),
+                    "peak_kind": f"{kind} copy bandwidth", "traffic": None,
+                    "bytes_per_launch": nbytes, "ms_per_launch": round(sweep_ms, 5),
+                    "gather_share": round(gather_ms / sweep_ms, 4),
+                    "largest_gather_layer": big + 1,
+                    "largest_gather_ms": round(float(kms[2 * big]), 5),
+                    "kernel_ms": [round(float(v), 5) for v in kms]}
+
+    solver.close()
+    if rank != 0:
+        if ws > 1:
+            import torch.distributed as dist
+
+            dist.destroy_process_group()
+        return 0
+    cpu = None
+    if not args.no_cpu and ws == 1:
+        cpu = cpu_oracle_sample(inst)
+    st0 = stats[-1]
+    line = {
+        "metric": "state-updates/s (solve to 1e-10 relative balance residual; N=24 time-to-tol, "
+                  "FP32+refinement vs plain FP64, reported beside it)",
+        "value": value, "unit": "state-updates/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+df64 (fp64 scalars)",
+        "data": "synthetic",
+        "config": {"workload": inst.name, "N": N, "J": J, "mode": I.MODE_NAMES[inst.mode],
+                   "load": round(inst.load, 4), "tol": args.tol, "precision": args.precision,
+                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                   "l2": "inputs larger than L2 (DF64 table 1.6 GB, FP32 table 0.8 GB)"},
+        "sweeps_per_step": {"fp32": st0["sweeps_fp32"], "hi": st0["sweeps_hi"]},
+        "time_to_tol_ms": compare or None,
+        "table_build_ms": st0["ms_table"],
+        "gpu_launches": launches, "clocks": clk, "roofline": roof, "e2e": e2e,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line))
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    if args.profile:
+        return run_profile(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,195 @@
+/*
+ * hq.h -- C ABI of the GB300 stationary solver for the spatial hypercube queue
+ * with heterogeneous service rates (Hua, Luo, Swersey & Wen, arXiv 2603.03019).
+ *
+ * Model (Section 2.1): N units, J demand nodes.  Calls from node j arrive as a
+ * Poisson stream of rate lambda_j (= lambda f_j) and go to the first idle unit on
+ * node j's preference list zeta_j; unit i serves at exponential rate nu_i.  A call
+ * that finds every unit busy is lost (HQ_LOSS), waits in a buffer of C places
+ * (HQ_FINITE, Proposition 2) or waits in an unbounded queue (HQ_INFINITE, the
+ * Remark after Proposition 2).  A state B is an N-bit mask, bit i = unit i busy
+ * ("y-order", Section 4.2: y(B) = sum_i b_i 2^(i-1) with 1-based units).
+ *
+ * Method: the conditional-probability reformulation (Proposition 1, Eq. 8-10) solved
+ * by the layer-by-layer iteration of Algorithm 1 (Eq. 12-14), with the upward
+ * rates of Eq. (3) built once per instance into a device-resident table.
+ *
+ * Conventions for every call:
+ *   - Return value: HQ_OK (0) or a negative hq_status.  No call throws, aborts or
+ *     exits.  hq_strerror() gives a static message; hq_last_error() gives the
+ *     last failing call's detail on this thread.
+ *   - Memory: arguments named *_mem say where the matching pointer lives:
+ *     HQ_HOST (ordinary or pinned host memory) or HQ_DEVICE (memory of the device
+ *     that was current when the solver was created).  The caller owns every
+ *     buffer it passes; the library copies inputs in and results out and keeps
+ *     no caller pointer after a call returns.
+ *   - The solver owns all device memory it allocates (hq_create) and frees it in
+ *     hq_destroy.  Calls on one handle must not overlap (thread-compatible, not
+ *     thread-safe); separate handles are independent.
+ *   - Every call returns after its device work has finished on the solver's
+ *     stream (the stream given to hq_create).
+ */
+#ifndef HQ_H_
+#define HQ_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  HQ_OK = 0,
+  HQ_EINVAL = -1,          /* bad argument or instance (see hq_last_error) */
+  HQ_ENOMEM = -2,          /* device allocation failed */
+  HQ_EUNSTABLE = -3,       /* infinite queue with lambda >= sum nu (Remark) */
+  HQ_ENOTCONVERGED = -4,   /* max_sweeps reached; results are readable */
+  HQ_EDIVERGED = -5,       /* non-finite or growing iterate; results are not valid */
+  HQ_ETIMEOUT = -6,        /* a bounded device-side wait gave up */
+  HQ_ECUDA = -7,           /* a CUDA runtime call failed */
+  HQ_ESTATE = -8           /* call out of order (e.g. results before a solve) */
+} hq_status;
+
+typedef enum { HQ_LOSS = 0, HQ_FINITE = 1, HQ_INFINITE = 2 } hq_mode;
+typedef enum { HQ_HOST = 0, HQ_DEVICE = 1 } hq_mem;
+
+/* Arithmetic of the sweeps.  Layer totals lambda(n), mu(n), the within-layer
+ * solve, the birth-death step and the residual are FP64 in every mode. */
+typedef enum {
+  HQ_PREC_FP64 = 0,      /* IEEE double sweeps */
+  HQ_PREC_DF64 = 1,      /* double-float sweeps: values as (hi, lo) float pairs,
+                            48-bit significand, FP32 ALU */
+  HQ_PREC_FP32 = 2,      /* FP32 sweeps only (accuracy ~1e-6 relative) */
+  HQ_PREC_FP32_DF64 = 3, /* FP32 sweeps until they stall, then DF64 sweeps */
+  HQ_PREC_FP32_FP64 = 4  /* FP32 sweeps until they stall, then FP64 sweeps */
+} hq_precision;
+
+typedef enum {
+  HQ_TOL_STEP = 0,     /* max_{n,m} |p_n^k(B_m) - p_n^{k-1}(B_m)| <= tol (Algorithm 1's epsilon) */
+  HQ_TOL_RESIDUAL = 1  /* max_m |out_m - in_m| / max_m out_m of Eq. (1) <= tol, FP64 */
+} hq_tol_kind;
+
+typedef enum { HQ_WARM_NONE = 0, HQ_WARM_GIVEN = 1, HQ_WARM_MLP = 2 } hq_warm;
+
+typedef struct hq_opts {
+  double tol;          /* stopping tolerance (see tol_kind) */
+  int tol_kind;        /* hq_tol_kind */
+  int max_sweeps;      /* cap on outer iterations k (all precisions together) */
+  int precision;       /* hq_precision */
+  int check_every;     /* sweeps between host-side convergence checks (>= 1) */
+  int warm_start;      /* hq_warm */
+  int warm_mem;        /* hq_mem of warm_p */
+  const double* warm_p;/* HQ_WARM_GIVEN: start vector p_n(B) in y-order, length 2^N */
+  double fp32_stall;   /* mixed modes: leave FP32 when the step's decay per check is
+                          worse than this ratio (0 = default 0.9) */
+  int reserved[6];
+} hq_opts;
+
+typedef struct hq_stats {
+  int sweeps_fp32;        /* sweeps done in FP32 */
+  int sweeps_hi;          /* sweeps done in FP64 or DF64 */
+  int residual_checks;    /* FP64 residual evaluations */
+  int converged;          /* 1 if the tolerance was met */
+  double final_step;      /* last max |p^k - p^{k-1}| */
+  double final_residual;  /* last evaluated residual, -1 if none */
+  double ms_total;        /* wall time of hq_solve */
+  double ms_table;        /* wall time of the table build in the last hq_load */
+  double state_updates;   /* (2^N - 2) * total sweeps */
+  int warm_used;          /* 1 if a warm start was kept, 0 if cold (or fell back) */
+  int reserved[5];
+} hq_stats;
+
+typedef struct hq_solver hq_solver;
+
+/* Fill opts with defaults: tol 1e-10 on the residual, FP32 then DF64 sweeps,
+ * check every 8 sweeps, max 100000 sweeps, cold start. */
+void hq_default_opts(hq_opts* opts);
+
+/* Allocate a solver for N units (1..28), J nodes (>= 1) and a queue mode
+ * (capacity_C >= 1 iff HQ_FINITE, ignored otherwise) on the current device.
+ * stream: a cudaStream_t, or NULL for the default stream.  Allocates every device
+ * buffer the solve needs (about 16 N 2^N + 48 2^N bytes plus a (N/2) 2^N FP32
+ * table, e.g. 4.3 GB at N=24).  Builds the N-dependent layout (layer-ranked
+ * state masks and rank tables).  Writes the handle to *out. */
+int hq_create(int N, int J, int mode, int capacity_C, void* stream, hq_solver** out);
+
+/* Load an instance (Section 2.1) and build its upward-rate table (Eq. 3).
+ *   lambda_j: J doubles, lambda_j >= 0, sum > 0 (the per-node rates lambda f_j)
+ *   nu:       N doubles > 0 (service rates nu_i)
+ *   pref:     J*N int32, row-major; row j = zeta_j as 0-based unit ids, each row
+ *             a permutation of 0..N-1
+ * All three live in memory `mem`.  Validates (HQ_EINVAL / HQ_EUNSTABLE), copies
+ * the inputs to the device and builds the table by a subset-sum transform over
+ * the preference prefixes.  Discards any previous solution. */
+int hq_load(hq_solver* h, const double* lambda_j, const double* nu, const int32_t* pref,
+            int mem);
+
+/* Algorithm 1 to the tolerance in opts (NULL = defaults).  Returns HQ_OK,
+ * HQ_ENOTCONVERGED (results readable), HQ_EDIVERGED or an error.  stats may be
+ * NULL.  After it returns, the result getters below are valid. */
+int hq_solve(hq_solver* h, const hq_opts* opts, hq_stats* stats);
+
+/* P{B} = p(w(B)) p_{w(B)}(B) (Proposition 1) for all 2^N states, y-order. */
+int hq_get_stationary(hq_solver* h, double* P, int mem);
+
+/* p(n), the birth-death distribution of the number of calls in the system
+ * (Eq. 10 / Proposition 2): N+1 values (loss, infinite) or N+C+1 (finite).  For
+ * HQ_INFINITE, queue[0] receives sum_{c>=1} P~{c} if queue != NULL. */
+int hq_get_layer_marginals(hq_solver* h, double* pn, double* queue_tail, int mem);
+
+/* Conditional probabilities p_n(B) (each layer sums to 1), y-order, 2^N values. */
+int hq_get_conditional(hq_solver* h, double* p, int mem);
+
+/* rho_i: fraction of time unit i is busy (queued states count as busy), N values. */
+int hq_get_utilisation(hq_solver* h, double* rho, int mem);
+
+/* R[j*N + i]: probability that a call from node j is served by unit i (J x N).
+ * Calls that wait are served by the unit that frees first: unit i w.p.
+ * nu_i / sum nu.  Rows sum to 1 - P(call lost). */
+int hq_get_response_pattern(hq_solver* h, double* R, int mem);
+
+/* W[i*J + j] = lambda_j R_ji / nu_i: fraction of time unit i serves node j (N x J). */
+int hq_get_workload(hq_solver* h, double* W, int mem);
+
+/* Scalars: out[0] throughput sum_i nu_i rho_i, out[1] P(call lost),
+ * out[2] P(call waits), out[3] relative balance residual of the returned P,
+ * out[4] mean number of busy units. 5 doubles, host memory. */
+int hq_get_summary(hq_solver* h, double* out5);
+
+/* Pull-form upward-rate table in layer-ranked order, for checking: for layer
+ * n (1..N), state rank k (colex order inside the layer) and busy slot s (s-th
+ * busy unit in increasing id order), entry toff(n) + s*C(N,n) + k holds
+ * lambda_{l m} for l = B minus that unit (Eq. 3).  count = N 2^(N-1) doubles.
+ * Also writes the layer-ranked state masks (2^N uint32) if masks != NULL. */
+int hq_get_table(hq_solver* h, double* T, uint32_t* masks, int mem);
+
+/* Sizes of the solver: out[0]=N, [1]=J, [2]=mode, [3]=C, [4]=2^N,
+ * [5]=table entries, [6]=device bytes allocated.  8 int64 slots, host memory. */
+int hq_get_info(const hq_solver* h, int64_t* out8);
+
+/* Timing of the hot path: run `sweeps` outer iterations (Algorithm 1) of the current
+ * iterate in precision `precision` (HQ_PREC_FP64 / HQ_PREC_DF64 / HQ_PREC_FP32;
+ * the iterate is converted if needed), kernel by kernel, with CUDA events on the
+ * solver's stream around every launch.  ms_out (host, 2*(N-1) floats) receives the
+ * mean duration of the gather and update kernels of each layer n = 1..N-1, in
+ * order [gather_1, update_1, gather_2, ...].  The iterate advances by `sweeps`
+ * iterations; call hq_solve again for results.  Needs a previous hq_solve. */
+int hq_profile_sweep(hq_solver* h, int precision, int sweeps, float* ms_out);
+
+/* Algorithmic HBM bytes of one outer iteration in `precision`: per state of
+ * layers 1..N-1, its n table entries, r_m, its state mask, one read and one write
+ * of p (neighbour layers are L2-resident and not counted).  Host double. */
+double hq_sweep_bytes(const hq_solver* h, int precision);
+
+void hq_destroy(hq_solver* h);
+const char* hq_strerror(int code);
+const char* hq_last_error(void);
+
+/* Device kernel launches made by the calling thread since the last reset (for
+ * accounting of the work the library does). */
+int64_t hq_launch_count(int reset);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HQ_H_ */

@@ -1,0 +1,509 @@
+// C ABI of the solver (include/hq.h): handle lifecycle, instance loading, the
+// outer loop of Algorithm 1 with its convergence checks, and result getters.
+#include <math.h>
+#include <string.h>
+
+#include <chrono>
+#include <string>
+
+#include "hq_internal.cuh"
+
+static thread_local std::string g_last_error;
+static thread_local int64_t g_launches = 0;
+
+void hq_set_error(const std::string& msg) { g_last_error = msg; }
+
+int hq_cuda_fail(cudaError_t e, const char* what, const char* file, int line) {
+  g_last_error = std::string(what) + ": " + cudaGetErrorString(e) + " (" + file + ":" +
+                 std::to_string(line) + ")";
+  return e == cudaErrorMemoryAllocation ? HQ_ENOMEM : HQ_ECUDA;
+}
+
+void hq_count_launch(int64_t k) { g_launches += k; }
+
+extern "C" int64_t hq_launch_count(int reset) {
+  int64_t v = g_launches;
+  if (reset) g_launches = 0;
+  return v;
+}
+
+extern "C" const char* hq_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" const char* hq_strerror(int code) {
+  switch (code) {
+    case HQ_OK: return "ok";
+    case HQ_EINVAL: return "invalid argument or instance";
+    case HQ_ENOMEM: return "device memory allocation failed";
+    case HQ_EUNSTABLE: return "infinite queue is unstable (lambda >= sum nu)";
+    case HQ_ENOTCONVERGED: return "tolerance not reached within max_sweeps";
+    case HQ_EDIVERGED: return "iteration produced a non-finite or diverging iterate";
+    case HQ_ETIMEOUT: return "a bounded device wait timed out";
+    case HQ_ECUDA: return "CUDA runtime error";
+    case HQ_ESTATE: return "call out of order";
+    default: return "unknown status";
+  }
+}
+
+extern "C" void hq_default_opts(hq_opts* o) {
+  memset(o, 0, sizeof(*o));
+  o->tol = 1e-10;
+  o->tol_kind = HQ_TOL_RESIDUAL;
+  o->max_sweeps = 100000;
+  o->precision = HQ_PREC_FP32_DF64;
+  o->check_every = 8;
+  o->warm_start = HQ_WARM_NONE;
+  o->warm_mem = HQ_HOST;
+  o->warm_p = nullptr;
+  o->fp32_stall = 0.9;
+}
+
+static void free_all(hq_solver* h) {
+  void* ptrs[] = {h->masks, h->RL, h->RH, h->lam_j, h->nu, h->pref, h->pre, h->zeta,
+                  h->b64.T, h->b64.r, h->b64.p, h->b64.nu, h->bdf.T, h->bdf.r, h->bdf.p, h->bdf.nu,
+                  h->b32.T, h->b32.r, h->b32.p, h->b32.nu, h->ab, h->partials, h->sc, h->dflag,
+                  h->P, h->pn, h->rho, h->R, h->W, h->summary, h->pcond};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (h->hsc) cudaFreeHost(h->hsc);
+  for (int i = 0; i < 3; i++)
+    if (h->graph[i]) cudaGraphExecDestroy(h->graph[i]);
+  if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+}
+
+template <class T>
+static int dalloc(hq_solver* h, T** p, int64_t bytes) {
+  if (bytes <= 0) bytes = 16;
+  cudaError_t e = cudaMalloc((void**)p, (size_t)bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    hq_set_error("cudaMalloc of " + std::to_string(bytes) + " bytes failed: " +
+                 cudaGetErrorString(e));
+    return HQ_ENOMEM;
+  }
+  h->dev_bytes += bytes;
+  return HQ_OK;
+}
+
+#define HQ_TRY(x)            \
+  do {                       \
+    int rc_ = (x);           \
+    if (rc_ != HQ_OK) {      \
+      free_all(h);           \
+      delete h;              \
+      return rc_;            \
+    }                        \
+  } while (0)
+
+extern "C" int hq_create(int N, int J, int mode, int capacity_C, void* stream, hq_solver** out) {
+  if (!out) { hq_set_error("out is NULL"); return HQ_EINVAL; }
+  *out = nullptr;
+  if (N < 1 || N > HQ_MAXN) { hq_set_error("N must be in 1..28"); return HQ_EINVAL; }
+  if (J < 1) { hq_set_error("J must be >= 1"); return HQ_EINVAL; }
+  if (mode < HQ_LOSS || mode > HQ_INFINITE) { hq_set_error("mode must be 0, 1 or 2"); return HQ_EINVAL; }
+  if (mode == HQ_FINITE && (capacity_C < 1 || capacity_C > (1 << 20))) {
+    hq_set_error("finite buffer needs 1 <= C <= 2^20");
+    return HQ_EINVAL;
+  }
+  hq_solver* h = new hq_solver();
+  h->N = N;
+  h->J = J;
+  h->mode = mode;
+  h->C = mode == HQ_FINITE ? capacity_C : 0;
+  cudaGetDevice(&h->dev);
+  h->stream = (cudaStream_t)stream;
+  if (!h->stream) {
+    // graphs cannot be captured on the legacy default stream: use a stream of our own
+    if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      delete h;
+      hq_set_error("cudaStreamCreateWithFlags failed");
+      return HQ_ECUDA;
+    }
+    h->own_stream = true;
+  }
+  h->S = (int64_t)1 << N;
+  h->off[0] = 0;
+  h->toff[0] = 0;
+  h->max_layer = 0;
+  for (int n = 0; n <= N; n++) {
+    h->lsize[n] = (int64_t)hq_binom(N, n);
+    h->off[n + 1] = h->off[n] + h->lsize[n];
+    h->toff[n + 1] = h->toff[n] + (int64_t)n * h->lsize[n];
+    if (h->lsize[n] > h->max_layer) h->max_layer = h->lsize[n];
+  }
+  for (int n = N + 2; n < HQ_MAXN + 2; n++) {
+    h->off[n] = h->off[N + 1];
+    h->toff[n] = h->toff[N + 1];
+  }
+  h->tentries = h->toff[N + 1];
+  h->L = N < HQ_LO_BITS ? N : HQ_LO_BITS;
+  h->H = N - h->L;
+  const int64_t S = h->S, TE = h->tentries, half = S / 2 > 0 ? S / 2 : 1;
+  HQ_TRY(dalloc(h, &h->masks, S * 4));
+  HQ_TRY(dalloc(h, &h->RL, (int64_t)4 << h->L));
+  HQ_TRY(dalloc(h, &h->RH, ((int64_t)4 << h->H) * (h->L + 1)));
+  HQ_TRY(dalloc(h, &h->lam_j, (int64_t)J * 8));
+  HQ_TRY(dalloc(h, &h->nu, (int64_t)N * 8));
+  HQ_TRY(dalloc(h, &h->pref, (int64_t)J * N * 4));
+  HQ_TRY(dalloc(h, &h->pre, (int64_t)J * N * 4));
+  HQ_TRY(dalloc(h, &h->zeta, half * N * 8));
+  HQ_TRY(dalloc(h, (double**)&h->b64.T, TE * 8));
+  HQ_TRY(dalloc(h, (float2**)&h->bdf.T, TE * 8));
+  HQ_TRY(dalloc(h, (float**)&h->b32.T, TE * 4));
+  HQ_TRY(dalloc(h, (double**)&h->b64.r, S * 8));
+  HQ_TRY(dalloc(h, (float2**)&h->bdf.r, S * 8));
+  HQ_TRY(dalloc(h, (float**)&h->b32.r, S * 4));
+  HQ_TRY(dalloc(h, (double**)&h->b64.p, S * 8));
+  HQ_TRY(dalloc(h, (float2**)&h->bdf.p, S * 8));
+  HQ_TRY(dalloc(h, (float**)&h->b32.p, S * 4));
+  HQ_TRY(dalloc(h, (double**)&h->b64.nu, (int64_t)HQ_MAXN * 8));
+  HQ_TRY(dalloc(h, (float2**)&h->bdf.nu, (int64_t)HQ_MAXN * 8));
+  HQ_TRY(dalloc(h, (float**)&h->b32.nu, (int64_t)HQ_MAXN * 4));
+  HQ_TRY(dalloc(h, (double**)&h->ab, h->max_layer * 16));
+  int64_t blocks = (h->max_layer + HQ_THREADS - 1) / HQ_THREADS;
+  h->partials_len = blocks * 2 > 152 * 8 * HQ_MAXN ? blocks * 2 : 152 * 8 * HQ_MAXN;
+  HQ_TRY(dalloc(h, &h->partials, h->partials_len * 8));
+  HQ_TRY(dalloc(h, &h->sc, (int64_t)sizeof(DevScalars)));
+  HQ_TRY(dalloc(h, &h->dflag, 16));
+  HQ_TRY(dalloc(h, &h->P, S * 8));
+  HQ_TRY(dalloc(h, &h->pcond, S * 8));
+  HQ_TRY(dalloc(h, &h->pn, (int64_t)(N + h->C + 1) * 8));
+  HQ_TRY(dalloc(h, &h->rho, (int64_t)N * 8));
+  HQ_TRY(dalloc(h, &h->R, (int64_t)J * N * 8));
+  HQ_TRY(dalloc(h, &h->W, (int64_t)J * N * 8));
+  HQ_TRY(dalloc(h, &h->summary, 16 * 8));
+  if (cudaMallocHost((void**)&h->hsc, sizeof(DevScalars)) != cudaSuccess) {
+    cudaGetLastError();
+    free_all(h);
+    delete h;
+    hq_set_error("cudaMallocHost failed");
+    return HQ_ENOMEM;
+  }
+  cudaError_t e = cudaMemsetAsync(h->sc, 0, sizeof(DevScalars), h->stream);
+  if (e != cudaSuccess) {
+    int rc = hq_cuda_fail(e, "cudaMemsetAsync", __FILE__, __LINE__);
+    free_all(h);
+    delete h;
+    return rc;
+  }
+  HQ_TRY(hq_build_layout(h));
+  e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) {
+    int rc = hq_cuda_fail(e, "layout build", __FILE__, __LINE__);
+    free_all(h);
+    delete h;
+    return rc;
+  }
+  *out = h;
+  return HQ_OK;
+}
+
+extern "C" void hq_destroy(hq_solver* h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->stream);
+  free_all(h);
+  delete h;
+}
+
+static cudaMemcpyKind kind_in(int mem) {
+  return mem == HQ_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+}
+static cudaMemcpyKind kind_out(int mem) {
+  return mem == HQ_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+}
+
+extern "C" int hq_load(hq_solver* h, const double* lambda_j, const double* nu, const int32_t* pref,
+                       int mem) {
+  if (!h || !lambda_j || !nu || !pref) { hq_set_error("NULL argument"); return HQ_EINVAL; }
+  if (mem != HQ_HOST && mem != HQ_DEVICE) { hq_set_error("mem must be HQ_HOST or HQ_DEVICE"); return HQ_EINVAL; }
+  auto t0 = std::chrono::steady_clock::now();
+  h->loaded = false;
+  h->solved = false;
+  HQ_CUDA(cudaMemcpyAsync(h->lam_j, lambda_j, sizeof(double) * h->J, kind_in(mem), h->stream));
+  HQ_CUDA(cudaMemcpyAsync(h->nu, nu, sizeof(double) * h->N, kind_in(mem), h->stream));
+  HQ_CUDA(cudaMemcpyAsync(h->pref, pref, sizeof(int32_t) * h->J * h->N, kind_in(mem), h->stream));
+  int rc = hq_validate_device(h);
+  if (rc != HQ_OK) return rc;
+  if (!(h->lam > 0.0)) { hq_set_error("sum of lambda_j must be > 0"); return HQ_EINVAL; }
+  if (h->mode == HQ_INFINITE && !(h->lam < h->nu_sum)) {
+    hq_set_error("infinite queue needs lambda < sum nu_i");
+    return HQ_EUNSTABLE;
+  }
+  HQ_CUDA(cudaMemcpyAsync(&h->sc->lam, &h->lam, sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  rc = hq_build_table(h);
+  if (rc != HQ_OK) return rc;
+  rc = hq_build_rates(h);
+  if (rc != HQ_OK) return rc;
+  HQ_CUDA(cudaStreamSynchronize(h->stream));
+  h->ms_table = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  h->loaded = true;
+  h->cur_prec = -1;
+  return HQ_OK;
+}
+
+static int pull_scalars(hq_solver* h) {
+  HQ_CUDA(cudaMemcpyAsync(h->hsc, h->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, h->stream));
+  HQ_CUDA(cudaStreamSynchronize(h->stream));
+  return HQ_OK;
+}
+
+extern "C" int hq_solve(hq_solver* h, const hq_opts* opts_in, hq_stats* stats) {
+  if (!h) { hq_set_error("NULL solver"); return HQ_EINVAL; }
+  if (!h->loaded) { hq_set_error("hq_load has not succeeded"); return HQ_ESTATE; }
+  hq_opts o;
+  if (opts_in) o = *opts_in;
+  else hq_default_opts(&o);
+  if (o.check_every < 1) o.check_every = 1;
+  if (o.max_sweeps < 0) { hq_set_error("max_sweeps must be >= 0"); return HQ_EINVAL; }
+  if (o.precision < HQ_PREC_FP64 || o.precision > HQ_PREC_FP32_FP64) { hq_set_error("bad precision"); return HQ_EINVAL; }
+  if (o.tol_kind != HQ_TOL_STEP && o.tol_kind != HQ_TOL_RESIDUAL) { hq_set_error("bad tol_kind"); return HQ_EINVAL; }
+  if (o.warm_start == HQ_WARM_GIVEN && !o.warm_p) { hq_set_error("warm_p is NULL"); return HQ_EINVAL; }
+  if (o.warm_start == HQ_WARM_MLP) { hq_set_error("no warm-start model is attached"); return HQ_EINVAL; }
+  double stall = o.fp32_stall > 0.0 ? o.fp32_stall : 0.9;
+  auto t0 = std::chrono::steady_clock::now();
+
+  int phases[2];
+  int nph = 1;
+  switch (o.precision) {
+    case HQ_PREC_FP64: phases[0] = HQ_PREC_FP64; break;
+    case HQ_PREC_DF64: phases[0] = HQ_PREC_DF64; break;
+    case HQ_PREC_FP32: phases[0] = HQ_PREC_FP32; break;
+    case HQ_PREC_FP32_DF64: phases[0] = HQ_PREC_FP32; phases[1] = HQ_PREC_DF64; nph = 2; break;
+    default: phases[0] = HQ_PREC_FP32; phases[1] = HQ_PREC_FP64; nph = 2; break;
+  }
+  int ph = 0;
+  int rc = hq_init_iterate(h, phases[0], o.warm_start == HQ_WARM_GIVEN ? o.warm_p : nullptr,
+                           o.warm_mem);
+  if (rc != HQ_OK) return rc;
+  h->solved = false;
+
+  int sweeps[2] = {0, 0};
+  int total = 0, checks = 0, res_checks = 0, since_res = 0, stalled = 0;
+  double step = INFINITY, prev_check_step = 0.0;
+  double res = -1.0, res_at_step = 0.0;
+  bool converged = false;
+  int status = HQ_OK;
+  if (h->N == 1) {
+    converged = true;  // no layer between the empty and the full state
+    step = 0.0;
+  }
+  while (!converged && total < o.max_sweeps) {
+    const int prec = phases[ph];
+    cudaGraphExec_t g;
+    int nk = 0;
+    rc = hq_get_sweep_graph(h, prec, &g, &nk);
+    if (rc != HQ_OK) return rc;
+    int nrun = o.check_every;
+    if (nrun > o.max_sweeps - total) nrun = o.max_sweeps - total;
+    for (int i = 0; i < nrun; i++) {
+      HQ_CUDA(cudaGraphLaunch(g, h->stream));
+      hq_count_launch(nk);
+    }
+    rc = pull_scalars(h);
+    if (rc != HQ_OK) return rc;
+    total += nrun;
+    sweeps[prec == HQ_PREC_FP32 ? 0 : 1] += nrun;
+    checks++;
+    step = h->hsc->step;
+    if ((h->hsc->flags & 1) || !isfinite(step)) {
+      hq_set_error("non-finite value in the iteration");
+      status = HQ_EDIVERGED;
+      break;
+    }
+    const double ratio = prev_check_step > 0.0 ? step / prev_check_step : 0.0;
+    const bool last_phase = ph == nph - 1;
+    if (!last_phase) {
+      // leave FP32 once its steps stop shrinking geometrically (rounding floor)
+      if ((prev_check_step > 0.0 && ratio > stall) || step == 0.0) {
+        rc = hq_convert_iterate(h, phases[ph], phases[ph + 1]);
+        if (rc != HQ_OK) return rc;
+        ph++;
+        prev_check_step = 0.0;
+        continue;
+      }
+      prev_check_step = step;
+      continue;
+    }
+    if (o.tol_kind == HQ_TOL_STEP) {
+      if (step <= o.tol) converged = true;
+    } else {
+      bool do_check = res < 0.0 || since_res >= 8 || step == 0.0;
+      if (!do_check && res_at_step > 0.0) {
+        double predicted = res * (step / res_at_step);
+        do_check = predicted <= 4.0 * o.tol;
+      }
+      if (do_check) {
+        rc = hq_compute_residual(h, &res);
+        if (rc != HQ_OK) return rc;
+        res_checks++;
+        res_at_step = step;
+        since_res = 0;
+        if (res <= o.tol) converged = true;
+      } else {
+        since_res++;
+      }
+    }
+    // a precision floor that the tolerance lies below: stop instead of spinning
+    if (!converged && prev_check_step > 0.0 && ratio >= 1.0) {
+      if (++stalled >= 4) break;
+    } else {
+      stalled = 0;
+    }
+    prev_check_step = step;
+  }
+  if (status == HQ_EDIVERGED) {
+    if (stats) {
+      memset(stats, 0, sizeof(*stats));
+      stats->sweeps_fp32 = sweeps[0];
+      stats->sweeps_hi = sweeps[1];
+      stats->final_step = step;
+      stats->final_residual = -1.0;
+    }
+    return status;
+  }
+  double final_res = -1.0;
+  rc = hq_finalize(h, phases[ph], true, &final_res);
+  if (rc != HQ_OK) return rc;
+  h->solved = true;
+  if (!converged) status = HQ_ENOTCONVERGED;
+  if (stats) {
+    memset(stats, 0, sizeof(*stats));
+    stats->sweeps_fp32 = sweeps[0];
+    stats->sweeps_hi = sweeps[1];
+    stats->residual_checks = res_checks;
+    stats->converged = converged ? 1 : 0;
+    stats->final_step = step;
+    stats->final_residual = final_res;
+    stats->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    stats->ms_table = h->ms_table;
+    stats->state_updates = (double)(h->S - 2) * (double)total;
+    stats->warm_used = o.warm_start != HQ_WARM_NONE ? 1 : 0;
+  }
+  (void)checks;
+  return status;
+}
+
+static int need_solved(const hq_solver* h) {
+  if (!h) { hq_set_error("NULL solver"); return HQ_EINVAL; }
+  if (!h->solved) { hq_set_error("no solution yet (call hq_solve)"); return HQ_ESTATE; }
+  return HQ_OK;
+}
+
+static int copy_out(hq_solver* h, void* dst, const void* src, int64_t bytes, int mem) {
+  if (!dst) { hq_set_error("NULL output"); return HQ_EINVAL; }
+  if (mem != HQ_HOST && mem != HQ_DEVICE) { hq_set_error("mem must be HQ_HOST or HQ_DEVICE"); return HQ_EINVAL; }
+  HQ_CUDA(cudaMemcpyAsync(dst, src, (size_t)bytes, kind_out(mem), h->stream));
+  HQ_CUDA(cudaStreamSynchronize(h->stream));
+  return HQ_OK;
+}
+
+extern "C" int hq_get_stationary(hq_solver* h, double* P, int mem) {
+  int rc = need_solved(h);
+  if (rc != HQ_OK) return rc;
+  return copy_out(h, P, h->P, h->S * 8, mem);
+}
+
+extern "C" int hq_get_conditional(hq_solver* h, double* p, int mem) {
+  int rc = need_solved(h);
+  if (rc != HQ_OK) return rc;
+  return copy_out(h, p, h->pcond, h->S * 8, mem);
+}
+
+extern "C" int hq_get_layer_marginals(hq_solver* h, double* pn, double* queue_tail, int mem) {
+  int rc = need_solved(h);
+  if (rc != HQ_OK) return rc;
+  rc = copy_out(h, pn, h->pn, (int64_t)(h->N + h->C + 1) * 8, mem);
+  if (rc != HQ_OK) return rc;
+  if (queue_tail) rc = copy_out(h, queue_tail, h->summary + 7, 8, mem);
+  return rc;
+}
+
+extern "C" int hq_get_utilisation(hq_solver* h, double* rho, int mem) {
+  int rc = need_solved(h);
+  if (rc != HQ_OK) return rc;
+  return copy_out(h, rho, h->rho, (int64_t)h->N * 8, mem);
+}
+
+extern "C" int hq_get_response_pattern(hq_solver* h, double* R, int mem) {
+  int rc = need_solved(h);
+  if (rc != HQ_OK) return rc;
+  return copy_out(h, R, h->R, (int64_t)h->J * h->N * 8, mem);
+}
+
+extern "C" int hq_get_workload(hq_solver* h, double* W, int mem) {
+  int rc = need_solved(h);
+  if (rc != HQ_OK) return rc;
+  return copy_out(h, W, h->W, (int64_t)h->J * h->N * 8, mem);
+}
+
+extern "C" int hq_get_summary(hq_solver* h, double* out5) {
+  int rc = need_solved(h);
+  if (rc != HQ_OK) return rc;
+  return copy_out(h, out5, h->summary, 5 * 8, HQ_HOST);
+}
+
+extern "C" int hq_get_table(hq_solver* h, double* T, uint32_t* masks, int mem) {
+  if (!h) { hq_set_error("NULL solver"); return HQ_EINVAL; }
+  if (!h->loaded) { hq_set_error("hq_load has not succeeded"); return HQ_ESTATE; }
+  int rc = HQ_OK;
+  if (T) rc = copy_out(h, T, h->b64.T, h->tentries * 8, mem);
+  if (rc == HQ_OK && masks) rc = copy_out(h, masks, h->masks, h->S * 4, mem);
+  return rc;
+}
+
+extern "C" int hq_get_info(const hq_solver* h, int64_t* out8) {
+  if (!h || !out8) { hq_set_error("NULL argument"); return HQ_EINVAL; }
+  out8[0] = h->N;
+  out8[1] = h->J;
+  out8[2] = h->mode;
+  out8[3] = h->C;
+  out8[4] = h->S;
+  out8[5] = h->tentries;
+  out8[6] = h->dev_bytes;
+  out8[7] = h->max_layer;
+  return HQ_OK;
+}
+
+extern "C" double hq_sweep_bytes(const hq_solver* h, int precision) {
+  if (!h) return 0.0;
+  const double e = precision == HQ_PREC_FP32 ? 4.0 : 8.0;
+  double b = 0.0;
+  for (int n = 1; n <= h->N - 1; n++) b += (double)h->lsize[n] * ((n + 3) * e + 4.0);
+  return b;
+}
+
+extern "C" int hq_profile_sweep(hq_solver* h, int precision, int sweeps, float* ms_out) {
+  int rc = need_solved(h);
+  if (rc != HQ_OK) return rc;
+  if (!ms_out || sweeps < 1) { hq_set_error("ms_out NULL or sweeps < 1"); return HQ_EINVAL; }
+  if (precision != HQ_PREC_FP64 && precision != HQ_PREC_DF64 && precision != HQ_PREC_FP32) {
+    hq_set_error("precision must be FP64, DF64 or FP32");
+    return HQ_EINVAL;
+  }
+  const int N = h->N;
+  for (int i = 0; i < 2 * (N - 1); i++) ms_out[i] = 0.f;
+  if (N < 2) return HQ_OK;
+  if (h->cur_prec != precision) {
+    rc = hq_convert_iterate(h, h->cur_prec, precision);
+    if (rc != HQ_OK) return rc;
+  }
+  const int nev = 2 * (N - 1) + 1;
+  cudaEvent_t ev[2 * HQ_MAXN + 1];
+  for (int i = 0; i < nev; i++) HQ_CUDA(cudaEventCreate(&ev[i]));
+  for (int s = 0; s < sweeps && rc == HQ_OK; s++) {
+    rc = hq_launch_sweep_timed(h, precision, ev);
+    if (rc != HQ_OK) break;
+    cudaError_t e = cudaEventSynchronize(ev[nev - 1]);
+    if (e != cudaSuccess) { rc = hq_cuda_fail(e, "cudaEventSynchronize", __FILE__, __LINE__); break; }
+    for (int i = 0; i + 1 < nev; i++) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, ev[i], ev[i + 1]);
+      ms_out[i] += ms / (float)sweeps;
+    }
+  }
+  for (int i = 0; i < nev; i++) cudaEventDestroy(ev[i]);
+  if (rc == HQ_OK) {
+    HQ_CUDA(cudaStreamSynchronize(h->stream));
+  }
+  return rc;
+}

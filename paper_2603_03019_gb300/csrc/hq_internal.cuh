@@ -1,0 +1,259 @@
+// Internal declarations shared by the CUDA translation units of the hypercube
+// queue solver.  Not part of the public ABI (see include/hq.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/hq.h"
+
+#define HQ_MAXN 28
+#define HQ_LO_BITS 12          // low-part width of the split rank tables
+#define HQ_THREADS 256         // threads per CTA of the streaming kernels
+
+// ---------------------------------------------------------------------------
+// error plumbing (host)
+// ---------------------------------------------------------------------------
+void hq_set_error(const std::string& msg);
+int hq_cuda_fail(cudaError_t e, const char* what, const char* file, int line);
+void hq_count_launch(int64_t k = 1);
+
+#define HQ_CUDA(call)                                                   \
+  do {                                                                  \
+    cudaError_t e_ = (call);                                            \
+    if (e_ != cudaSuccess) return hq_cuda_fail(e_, #call, __FILE__, __LINE__); \
+  } while (0)
+
+#define HQ_LAUNCHED()                                                   \
+  do {                                                                  \
+    cudaError_t e_ = cudaGetLastError();                                \
+    if (e_ != cudaSuccess) return hq_cuda_fail(e_, "kernel launch", __FILE__, __LINE__); \
+    hq_count_launch();                                                  \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// double-float ("DF64") arithmetic: a value is hi + lo with two floats.
+// All steps use round-to-nearest intrinsics so that the compiler cannot fuse
+// them into FMAs (the error-free transforms rely on each rounding).
+// TwoSum (Knuth) and TwoProduct via FMA are the classical error-free
+// transforms of Dekker (1971) and Knuth (TAOCP vol. 2).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 df_fast_two_sum(float a, float b) {
+  float s = __fadd_rn(a, b);
+  float e = __fsub_rn(b, __fsub_rn(s, a));
+  return make_float2(s, e);
+}
+__device__ __forceinline__ float2 df_two_sum(float a, float b) {
+  float s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return make_float2(s, e);
+}
+__device__ __forceinline__ float2 df_norm(float2 a) { return df_fast_two_sum(a.x, a.y); }
+__device__ __forceinline__ float2 df_add(float2 a, float2 b) {
+  float2 s = df_two_sum(a.x, b.x);
+  float e = __fadd_rn(s.y, __fadd_rn(a.y, b.y));
+  return df_fast_two_sum(s.x, e);
+}
+__device__ __forceinline__ float2 df_neg(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 df_sub(float2 a, float2 b) { return df_add(a, df_neg(b)); }
+__device__ __forceinline__ float2 df_mul(float2 a, float2 b) {
+  float p = __fmul_rn(a.x, b.x);
+  float e = fmaf(a.x, b.x, -p);
+  e = fmaf(a.x, b.y, e);
+  e = fmaf(a.y, b.x, e);
+  return df_fast_two_sum(p, e);
+}
+// acc += a * b with acc kept as an unnormalised pair (value = acc.x + acc.y)
+__device__ __forceinline__ void df_fma_acc(float2& acc, float2 a, float2 b) {
+  float p = __fmul_rn(a.x, b.x);
+  float pe = fmaf(a.x, b.x, -p);
+  pe = fmaf(a.x, b.y, pe);
+  pe = fmaf(a.y, b.x, pe);
+  float s = __fadd_rn(acc.x, p);
+  float bb = __fsub_rn(s, acc.x);
+  float err = __fadd_rn(__fsub_rn(acc.x, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  acc.x = s;
+  acc.y = __fadd_rn(acc.y, __fadd_rn(err, pe));
+}
+__device__ __forceinline__ float2 df_from_double(double x) {
+  float h = __double2float_rn(x);
+  float l = __double2float_rn(x - (double)h);
+  return make_float2(h, l);
+}
+__device__ __forceinline__ double df_to_double(float2 a) { return (double)a.x + (double)a.y; }
+
+// ---------------------------------------------------------------------------
+// arithmetic policies of the sweep: storage type V::T, accumulator V::A
+// ---------------------------------------------------------------------------
+struct PolF64 {
+  typedef double T;
+  static constexpr int kind = HQ_PREC_FP64;
+  __device__ static T zero() { return 0.0; }
+  __device__ static void fma_acc(T& acc, T a, T b) { acc = fma(a, b, acc); }
+  __device__ static T mul(T a, T b) { return a * b; }
+  __device__ static T add(T a, T b) { return a + b; }
+  __device__ static T sub(T a, T b) { return a - b; }
+  __device__ static T norm(T a) { return a; }
+  __device__ static T from_d(double x) { return x; }
+  __device__ static double to_d(T a) { return a; }
+  __device__ static double absdiff(T a, T b) { return fabs(a - b); }
+  __device__ static T shfl_xor(T a, int m) { return __shfl_xor_sync(0xffffffffu, a, m); }
+};
+struct PolDF {
+  typedef float2 T;
+  static constexpr int kind = HQ_PREC_DF64;
+  __device__ static T zero() { return make_float2(0.f, 0.f); }
+  __device__ static void fma_acc(T& acc, T a, T b) { df_fma_acc(acc, a, b); }
+  __device__ static T mul(T a, T b) { return df_mul(a, b); }
+  __device__ static T add(T a, T b) { return df_add(a, b); }
+  __device__ static T sub(T a, T b) { return df_sub(a, b); }
+  __device__ static T norm(T a) { return df_norm(a); }
+  __device__ static T from_d(double x) { return df_from_double(x); }
+  __device__ static double to_d(T a) { return df_to_double(a); }
+  // |a - b| for nearby values: the hi difference is exact (Sterbenz), lo adds the rest
+  __device__ static double absdiff(T a, T b) {
+    return (double)fabsf(__fadd_rn(__fsub_rn(a.x, b.x), __fsub_rn(a.y, b.y)));
+  }
+  __device__ static T shfl_xor(T a, int m) {
+    return make_float2(__shfl_xor_sync(0xffffffffu, a.x, m), __shfl_xor_sync(0xffffffffu, a.y, m));
+  }
+};
+struct PolF32 {
+  typedef float T;
+  static constexpr int kind = HQ_PREC_FP32;
+  __device__ static T zero() { return 0.f; }
+  __device__ static void fma_acc(T& acc, T a, T b) { acc = fmaf(a, b, acc); }
+  __device__ static T mul(T a, T b) { return a * b; }
+  __device__ static T add(T a, T b) { return a + b; }
+  __device__ static T sub(T a, T b) { return a - b; }
+  __device__ static T norm(T a) { return a; }
+  __device__ static T from_d(double x) { return (float)x; }
+  __device__ static double to_d(T a) { return (double)a; }
+  __device__ static double absdiff(T a, T b) { return (double)fabsf(a - b); }
+  __device__ static T shfl_xor(T a, int m) { return __shfl_xor_sync(0xffffffffu, a, m); }
+};
+
+// ---------------------------------------------------------------------------
+// device-resident scalars of the iteration (all FP64)
+// ---------------------------------------------------------------------------
+struct DevScalars {
+  double lam_n[HQ_MAXN + 1];   // lambda^k(n)   (Eq. 13)
+  double mu_n[HQ_MAXN + 1];    // mu^k(n)       (Eq. 14, closed-form inner limit)
+  double c1[HQ_MAXN + 1];      // alpha mu* of the last update of layer n
+  double c2[HQ_MAXN + 1];      // beta of the last update of layer n
+  double step_layer[HQ_MAXN + 1];
+  double sum_layer[HQ_MAXN + 1];
+  double step;                 // max_n step_layer[n] of the last sweep
+  double step_prev;
+  int sweeps;                  // sweeps done on the device
+  int flags;                   // bit 0: non-finite value seen
+  unsigned ticket[4];          // last-block tickets
+  double red[16];              // results of whole-vector reductions
+  double lsum[HQ_MAXN + 1];    // sum_m p_n(B_m) per layer (whole-vector pass)
+  double lmu[HQ_MAXN + 1];     // sum_m mu_m p_n(B_m) per layer
+  double res_num[HQ_MAXN + 1]; // max_m |out_m - in_m| per layer (residual)
+  double res_den[HQ_MAXN + 1]; // max_m out_m per layer
+  double fac[HQ_MAXN + 1];     // P{B} = fac[w(B)] * p_w(B) after the birth-death step
+  double lam;                  // lambda = sum_j lambda_j of the loaded instance
+};
+
+// rank of a state from the split tables (see hq_layout.cu)
+__device__ __forceinline__ uint32_t hq_rank_split(const uint32_t* s_RL, const uint32_t* RH, int L,
+                                                  uint32_t x) {
+  uint32_t lo = x & ((1u << L) - 1u);
+  return s_RL[lo] + __ldg(RH + (size_t)(x >> L) * (L + 1) + __popc(lo));
+}
+
+// typed streaming / read-only loads
+__device__ __forceinline__ double ld_stream(const double* p) { return __ldcs(p); }
+__device__ __forceinline__ float2 ld_stream(const float2* p) { return __ldcs(p); }
+__device__ __forceinline__ float ld_stream(const float* p) { return __ldcs(p); }
+__device__ __forceinline__ double ld_ro(const double* p) { return __ldg(p); }
+__device__ __forceinline__ float2 ld_ro(const float2* p) { return __ldg(p); }
+__device__ __forceinline__ float ld_ro(const float* p) { return __ldg(p); }
+
+// per-precision vectors
+struct PrecBufs {
+  void* T = nullptr;   // pull-form table, toff layout
+  void* r = nullptr;   // 1/(lambda + mu_m), layer-ranked
+  void* p = nullptr;   // conditional p, layer-ranked
+  void* nu = nullptr;  // nu_i in this precision (N)
+};
+
+struct hq_solver {
+  int N = 0, J = 0, mode = 0, C = 0;
+  int dev = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int64_t S = 0;
+  int64_t off[HQ_MAXN + 2];    // layer n states: [off[n], off[n+1])
+  int64_t toff[HQ_MAXN + 2];   // table entries of layer n start at toff[n]
+  int64_t lsize[HQ_MAXN + 1];  // C(N, n)
+  int64_t tentries = 0;
+  int L = 0, H = 0;            // split rank tables: low L bits, high H bits
+  int64_t max_layer = 0;
+  int64_t dev_bytes = 0;
+  double lam = 0, nu_sum = 0;
+  bool loaded = false, solved = false;
+  int cur_prec = -1;           // precision holding the current iterate
+
+  // N-dependent layout
+  uint32_t* masks = nullptr;   // S, layer-ranked state masks
+  uint32_t* RL = nullptr;      // 2^L
+  uint32_t* RH = nullptr;      // 2^H x (L+1)
+  // instance
+  double* lam_j = nullptr;     // J
+  double* nu = nullptr;        // N
+  int32_t* pref = nullptr;     // J x N
+  uint32_t* pre = nullptr;     // J x N: units ranked before u by node j
+  double* zeta = nullptr;      // N x 2^(N-1) scratch of the subset-sum transforms
+  PrecBufs b64, bdf, b32;
+  void* ab = nullptr;          // per-layer (A, B) scratch, max_layer x 2 x 8 bytes
+  double* partials = nullptr;  // block partials of the reductions
+  int64_t partials_len = 0;
+  DevScalars* sc = nullptr;
+  DevScalars* hsc = nullptr;   // pinned host mirror
+  int* dflag = nullptr;        // device validation flag
+  // results
+  double* P = nullptr;         // S, y-order
+  double* pn = nullptr;        // N + C + 1
+  double* rho = nullptr;       // N
+  double* R = nullptr;         // J x N
+  double* W = nullptr;         // N x J
+  double* summary = nullptr;   // 8
+  double* pcond = nullptr;     // S, y-order conditional (normalised)
+  // sweep graphs per precision
+  cudaGraphExec_t graph[3] = {nullptr, nullptr, nullptr};
+  int graph_kernels[3] = {0, 0, 0};
+  double ms_table = 0;
+};
+
+// ---------------------------------------------------------------------------
+// kernels / launchers implemented across translation units
+// ---------------------------------------------------------------------------
+double hq_binom(int n, int k);
+
+// layout (hq_layout.cu)
+int hq_build_layout(hq_solver* h);
+int hq_validate_device(hq_solver* h);
+int hq_build_rates(hq_solver* h);  // r_m in all precisions
+
+// table (hq_table.cu)
+int hq_build_table(hq_solver* h);
+int hq_zeta_subset(hq_solver* h, double* buf, int bits, int count, bool superset);
+
+// sweep (hq_sweep.cu)
+int hq_init_iterate(hq_solver* h, int prec, const double* warm_y, int warm_mem);
+int hq_convert_iterate(hq_solver* h, int from, int to);
+int hq_launch_sweep(hq_solver* h, int prec);
+int hq_launch_sweep_timed(hq_solver* h, int prec, cudaEvent_t* ev);
+int hq_get_sweep_graph(hq_solver* h, int prec, cudaGraphExec_t* out, int* kernels);
+PrecBufs& hq_bufs(hq_solver* h, int prec);
+
+// results (hq_post.cu)
+int hq_layer_sums(hq_solver* h, int prec);
+int hq_finalize(hq_solver* h, int prec, bool full_outputs, double* residual_out);
+int hq_compute_residual(hq_solver* h, double* residual_out);

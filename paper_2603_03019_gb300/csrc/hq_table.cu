@@ -1,0 +1,209 @@
+// Upward transition rates of Eq. (3), built once per instance into a pull-form,
+// layer-ranked table.
+//
+// For a target state m with unit u busy, the rate of the upward move
+// (m - u) -> m is
+//     lambda_u(m - u) = sum_j lambda_j [all units node j ranks before u are busy in m]
+// (u is then node j's first idle unit in m - u: the reading of Eq. (3) stated in
+// the sentence that follows it, and the prefix walk of Algorithm 3).  With
+// pre_j(u) the set of units node j prefers to u and
+//     g_u(S) = sum_{j : pre_j(u) = S} lambda_j     (S a subset of the other N-1 units),
+// the rate is the subset sum F_u(X) = sum_{S subset of X} g_u(S) at X = m - u.  So the
+// whole table is N histograms plus N subset-sum (zeta) transforms over N-1 bits:
+// O(N^2 2^N) work independent of J, instead of one first-idle search per
+// (state, node) pair.  Sums are FP64; the emit writes FP64, double-float and FP32
+// copies in the pull layout
+//     T[toff(n) + s C(N,n) + k] = F_{c_s}(m_k - c_s),
+// m_k the rank-k state of layer n and c_s its s-th busy unit, so the sweep reads
+// slot s of consecutive states contiguously.
+#include "hq_internal.cuh"
+
+// remove bit u from x (x has bit u clear or it is ignored)
+__device__ __forceinline__ uint32_t squeeze_bit(uint32_t x, int u) {
+  uint32_t low = x & ((1u << u) - 1u);
+  return low | ((x >> (u + 1)) << u);
+}
+
+// pre[j*N + u] = units node j ranks before unit u
+__global__ void k_prefix_masks(int N, int J, const int32_t* pref, uint32_t* pre) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= J) return;
+  uint32_t acc = 0;
+  for (int h = 0; h < N; h++) {
+    int u = pref[(int64_t)j * N + h];
+    pre[(int64_t)j * N + u] = acc;
+    acc |= 1u << u;
+  }
+}
+
+// g_u histogram: one CTA per unit u.  Each node j whose key is new (no lower
+// j' shares it) sums lambda over all nodes with that key in increasing j, so the
+// result does not depend on thread timing.
+__global__ void k_histogram(int N, int J, const uint32_t* pre, const double* lam_j,
+                            double* zeta) {
+  int u = blockIdx.x;
+  int64_t half = (int64_t)1 << (N - 1);
+  double* F = zeta + (int64_t)u * half;
+  for (int j = threadIdx.x; j < J; j += blockDim.x) {
+    uint32_t key = squeeze_bit(__ldg(pre + (int64_t)j * N + u), u);
+    bool leader = true;
+    for (int jp = 0; jp < j && leader; jp++)
+      if (squeeze_bit(__ldg(pre + (int64_t)jp * N + u), u) == key) leader = false;
+    if (!leader) continue;
+    double s = 0.0;
+    for (int jp = j; jp < J; jp++)
+      if (squeeze_bit(__ldg(pre + (int64_t)jp * N + u), u) == key) s += __ldg(lam_j + jp);
+    F[key] = s;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// subset-sum (zeta) transform F(X) = sum_{S subset X} f(S), or the superset
+// version F(X) = sum_{S superset X} f(S), over `bits` bits for `count` arrays
+// laid end to end.  Pass 1 handles the low bits inside a shared-memory tile of
+// contiguous elements; later passes handle groups of high bits with tiles made
+// of 2^g strided rows of kCols contiguous elements.
+// ---------------------------------------------------------------------------
+constexpr int kTileLog = 12;           // 4096 doubles = 32 KB
+constexpr int kColsLog = 4;            // 16 contiguous doubles per row in later passes
+
+__global__ void k_zeta_low(double* buf, int bits, int tile_log, int64_t ntiles, bool superset) {
+  extern __shared__ double t[];
+  int64_t tile = blockIdx.x;
+  if (tile >= ntiles) return;
+  int64_t tsize = (int64_t)1 << tile_log;
+  double* base = buf + tile * tsize;
+  for (int64_t i = threadIdx.x; i < tsize; i += blockDim.x) t[i] = base[i];
+  __syncthreads();
+  int nb = bits < tile_log ? bits : tile_log;
+  for (int b = 0; b < nb; b++) {
+    int64_t bit = (int64_t)1 << b;
+    for (int64_t q = threadIdx.x; q < tsize / 2; q += blockDim.x) {
+      int64_t lo = ((q >> b) << (b + 1)) | (q & (bit - 1));
+      int64_t hi = lo | bit;
+      if (superset) t[lo] += t[hi];
+      else t[hi] += t[lo];
+    }
+    __syncthreads();
+  }
+  for (int64_t i = threadIdx.x; i < tsize; i += blockDim.x) base[i] = t[i];
+}
+
+// bits [b0, b0+g) of each array; tile = 2^g rows (stride 2^b0) x 2^cols_log columns
+__global__ void k_zeta_high(double* buf, int bits, int b0, int g, int cols_log, int64_t per_array,
+                            int64_t tiles_per_array, int count, bool superset) {
+  extern __shared__ double t[];
+  int64_t tid = blockIdx.x;
+  int a = (int)(tid / tiles_per_array);
+  if (a >= count) return;
+  int64_t tix = tid % tiles_per_array;
+  // tix enumerates (column block within 2^b0, position above b0+g)
+  int64_t colblocks = ((int64_t)1 << b0) >> cols_log;
+  int64_t cb = tix % colblocks;
+  int64_t above = tix / colblocks;
+  double* arr = buf + (int64_t)a * per_array;
+  int64_t start = (above << (b0 + g)) + (cb << cols_log);
+  int rows = 1 << g, cols = 1 << cols_log;
+  int64_t stride = (int64_t)1 << b0;
+  for (int i = threadIdx.x; i < rows * cols; i += blockDim.x) {
+    int r = i >> cols_log, c = i & (cols - 1);
+    t[i] = arr[start + r * stride + c];
+  }
+  __syncthreads();
+  for (int b = 0; b < g; b++) {
+    int bit = 1 << b;
+    for (int q = threadIdx.x; q < (rows / 2) * cols; q += blockDim.x) {
+      int rq = q >> cols_log, c = q & (cols - 1);
+      int rlo = ((rq >> b) << (b + 1)) | (rq & (bit - 1));
+      int rhi = rlo | bit;
+      int ilo = (rlo << cols_log) | c, ihi = (rhi << cols_log) | c;
+      if (superset) t[ilo] += t[ihi];
+      else t[ihi] += t[ilo];
+    }
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i < rows * cols; i += blockDim.x) {
+    int r = i >> cols_log, c = i & (cols - 1);
+    arr[start + r * stride + c] = t[i];
+  }
+  (void)bits;
+}
+
+int hq_zeta_subset(hq_solver* h, double* buf, int bits, int count, bool superset) {
+  if (bits <= 0) return HQ_OK;
+  int64_t per = (int64_t)1 << bits;
+  int tl = bits < kTileLog ? bits : kTileLog;
+  int64_t ntiles = (per >> tl) * count;
+  size_t smem = sizeof(double) << tl;
+  HQ_CUDA(cudaFuncSetAttribute(k_zeta_low, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024));
+  HQ_CUDA(cudaFuncSetAttribute(k_zeta_high, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024));
+  k_zeta_low<<<(unsigned)ntiles, 256, smem, h->stream>>>(buf, bits, tl, ntiles, superset);
+  HQ_LAUNCHED();
+  int b0 = tl;
+  while (b0 < bits) {
+    int g = bits - b0;
+    int cols_log = kColsLog < b0 ? kColsLog : b0;
+    int gmax = kTileLog - cols_log;
+    if (g > gmax) g = gmax;
+    int64_t colblocks = ((int64_t)1 << b0) >> cols_log;
+    int64_t above = per >> (b0 + g);
+    int64_t tpa = colblocks * above;
+    size_t sm = sizeof(double) << (g + cols_log);
+    k_zeta_high<<<(unsigned)(tpa * count), 256, sm, h->stream>>>(buf, bits, b0, g, cols_log, per,
+                                                                tpa, count, superset);
+    HQ_LAUNCHED();
+    b0 += g;
+  }
+  return HQ_OK;
+}
+
+struct EmitArgs {
+  int N;
+  int64_t off[HQ_MAXN + 2];
+  int64_t toff[HQ_MAXN + 2];
+};
+
+// one thread per state of layers 1..N: slot s <- F_{c_s}(m - c_s)
+__global__ void k_emit(EmitArgs a, int64_t S, const uint32_t* masks, const double* zeta,
+                       double* T64, float2* Tdf, float* T32) {
+  int64_t g = a.off[1] + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= S) return;
+  int n = 1;
+  while (n < a.N && a.off[n + 1] <= g) n++;
+  int64_t k = g - a.off[n];
+  int64_t Ln = a.off[n + 1] - a.off[n];
+  int64_t half = (int64_t)1 << (a.N - 1);
+  uint32_t x = masks[g];
+  int s = 0;
+  for (uint32_t y = x; y; y &= y - 1, s++) {
+    int u = __ffs(y) - 1;
+    double v = __ldg(zeta + (int64_t)u * half + squeeze_bit(x, u));
+    int64_t idx = a.toff[n] + (int64_t)s * Ln + k;
+    T64[idx] = v;
+    Tdf[idx] = df_from_double(v);
+    T32[idx] = (float)v;
+  }
+}
+
+int hq_build_table(hq_solver* h) {
+  const int N = h->N, J = h->J;
+  int64_t half = (int64_t)1 << (N - 1);
+  k_prefix_masks<<<(J + 255) / 256, 256, 0, h->stream>>>(N, J, h->pref, h->pre);
+  HQ_LAUNCHED();
+  HQ_CUDA(cudaMemsetAsync(h->zeta, 0, sizeof(double) * half * N, h->stream));
+  k_histogram<<<N, 256, 0, h->stream>>>(N, J, h->pre, h->lam_j, h->zeta);
+  HQ_LAUNCHED();
+  int rc = hq_zeta_subset(h, h->zeta, N - 1, N, false);
+  if (rc != HQ_OK) return rc;
+  EmitArgs a;
+  a.N = N;
+  for (int i = 0; i < HQ_MAXN + 2; i++) {
+    a.off[i] = h->off[i];
+    a.toff[i] = h->toff[i];
+  }
+  int64_t cnt = h->S - h->off[1];
+  k_emit<<<(unsigned)((cnt + 255) / 256), 256, 0, h->stream>>>(
+      a, h->S, h->masks, h->zeta, (double*)h->b64.T, (float2*)h->bdf.T, (float*)h->b32.T);
+  HQ_LAUNCHED();
+  return HQ_OK;
+}

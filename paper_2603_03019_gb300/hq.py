@@ -1,0 +1,316 @@
+"""Thin Python binding of the C ABI in include/hq.h (argument marshalling only).
+
+Every function keeps the C name and calls straight into libhq.so; all work runs in
+the library's CUDA kernels.  Arrays are numpy arrays (host memory, HQ_HOST) or
+torch CUDA tensors (device memory, HQ_DEVICE).  There is no CPU fallback: if the
+library cannot be built or loaded, ``load()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import threading
+
+import numpy as np
+
+from . import _build
+
+HQ_OK, HQ_EINVAL, HQ_ENOMEM, HQ_EUNSTABLE, HQ_ENOTCONVERGED = 0, -1, -2, -3, -4
+HQ_EDIVERGED, HQ_ETIMEOUT, HQ_ECUDA, HQ_ESTATE = -5, -6, -7, -8
+HQ_LOSS, HQ_FINITE, HQ_INFINITE = 0, 1, 2
+HQ_HOST, HQ_DEVICE = 0, 1
+HQ_PREC_FP64, HQ_PREC_DF64, HQ_PREC_FP32, HQ_PREC_FP32_DF64, HQ_PREC_FP32_FP64 = 0, 1, 2, 3, 4
+HQ_TOL_STEP, HQ_TOL_RESIDUAL = 0, 1
+HQ_WARM_NONE, HQ_WARM_GIVEN, HQ_WARM_MLP = 0, 1, 2
+
+PRECISION = {"fp64": HQ_PREC_FP64, "df64": HQ_PREC_DF64, "fp32": HQ_PREC_FP32,
+             "fp32+df64": HQ_PREC_FP32_DF64, "fp32+fp64": HQ_PREC_FP32_FP64}
+
+
+class hq_opts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("tol_kind", ctypes.c_int), ("max_sweeps", ctypes.c_int),
+                ("precision", ctypes.c_int), ("check_every", ctypes.c_int),
+                ("warm_start", ctypes.c_int), ("warm_mem", ctypes.c_int),
+                ("warm_p", ctypes.c_void_p), ("fp32_stall", ctypes.c_double),
+                ("reserved", ctypes.c_int * 6)]
+
+
+class hq_stats(ctypes.Structure):
+    _fields_ = [("sweeps_fp32", ctypes.c_int), ("sweeps_hi", ctypes.c_int),
+                ("residual_checks", ctypes.c_int), ("converged", ctypes.c_int),
+                ("final_step", ctypes.c_double), ("final_residual", ctypes.c_double),
+                ("ms_total", ctypes.c_double), ("ms_table", ctypes.c_double),
+                ("state_updates", ctypes.c_double), ("warm_used", ctypes.c_int),
+                ("reserved", ctypes.c_int * 5)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
+class HQError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{msg} (status {code})")
+        self.code = code
+
+
+_lib = None
+_lock = threading.Lock()
+_vp, _i, _d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+
+_SIGS = {
+    "hq_default_opts": (None, [ctypes.POINTER(hq_opts)]),
+    "hq_create": (_i, [_i, _i, _i, _i, _vp, ctypes.POINTER(_vp)]),
+    "hq_load": (_i, [_vp, _vp, _vp, _vp, _i]),
+    "hq_solve": (_i, [_vp, ctypes.POINTER(hq_opts), ctypes.POINTER(hq_stats)]),
+    "hq_get_stationary": (_i, [_vp, _vp, _i]),
+    "hq_get_layer_marginals": (_i, [_vp, _vp, _vp, _i]),
+    "hq_get_conditional": (_i, [_vp, _vp, _i]),
+    "hq_get_utilisation": (_i, [_vp, _vp, _i]),
+    "hq_get_response_pattern": (_i, [_vp, _vp, _i]),
+    "hq_get_workload": (_i, [_vp, _vp, _i]),
+    "hq_get_summary": (_i, [_vp, _vp]),
+    "hq_get_table": (_i, [_vp, _vp, _vp, _i]),
+    "hq_get_info": (_i, [_vp, _vp]),
+    "hq_destroy": (None, [_vp]),
+    "hq_strerror": (ctypes.c_char_p, [_i]),
+    "hq_last_error": (ctypes.c_char_p, []),
+    "hq_launch_count": (ctypes.c_int64, [_i]),
+    "hq_profile_sweep": (_i, [_vp, _i, _i, _vp]),
+    "hq_sweep_bytes": (_d, [_vp, _i]),
+}
+
+
+def load(build: bool = True):
+    """Build (if stale) and load libhq.so.  Raises if it cannot."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.build() if build else _build.LIB
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+        return lib
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def _check(rc: int, allow=(HQ_OK,)) -> int:
+    if rc not in allow:
+        lib = load()
+        raise HQError(rc, f"{lib.hq_strerror(rc).decode()}: {lib.hq_last_error().decode()}")
+    return rc
+
+
+def _ptr(a):
+    """(address, mem) of a numpy array or torch tensor."""
+    if a is None:
+        return None, HQ_HOST
+    if isinstance(a, np.ndarray):
+        assert a.flags["C_CONTIGUOUS"]
+        return a.ctypes.data, HQ_HOST
+    # torch tensor
+    assert a.is_contiguous()
+    return a.data_ptr(), (HQ_DEVICE if a.is_cuda else HQ_HOST)
+
+
+# ---- the C calls, same names ------------------------------------------------------------
+
+def hq_default_opts() -> hq_opts:
+    o = hq_opts()
+    load().hq_default_opts(ctypes.byref(o))
+    return o
+
+
+def hq_create(N: int, J: int, mode: int = HQ_LOSS, capacity_C: int = 0, stream=None) -> int:
+    h = _vp()
+    s = stream if isinstance(stream, int) or stream is None else stream.cuda_stream
+    _check(load().hq_create(N, J, mode, capacity_C, s, ctypes.byref(h)))
+    return h.value
+
+
+def hq_load(h: int, lambda_j, nu, pref) -> None:
+    pl, ml = _ptr(lambda_j)
+    pn, mn = _ptr(nu)
+    pp, mp = _ptr(pref)
+    if not (ml == mn == mp):
+        raise ValueError("lambda_j, nu and pref must live in the same memory")
+    _check(load().hq_load(h, pl, pn, pp, ml))
+
+
+def hq_solve(h: int, opts: hq_opts | None = None, allow_notconverged: bool = True) -> tuple[int, hq_stats]:
+    st = hq_stats()
+    allow = (HQ_OK, HQ_ENOTCONVERGED) if allow_notconverged else (HQ_OK,)
+    rc = load().hq_solve(h, ctypes.byref(opts) if opts is not None else None, ctypes.byref(st))
+    _check(rc, allow)
+    return rc, st
+
+
+def _get(fn, h, out, *extra):
+    p, m = _ptr(out)
+    _check(getattr(load(), fn)(h, p, *extra, m))
+    return out
+
+
+def hq_get_stationary(h, out):
+    return _get("hq_get_stationary", h, out)
+
+
+def hq_get_conditional(h, out):
+    return _get("hq_get_conditional", h, out)
+
+
+def hq_get_layer_marginals(h, out, tail=None):
+    p, m = _ptr(out)
+    pt, mt = _ptr(tail)
+    _check(load().hq_get_layer_marginals(h, p, pt, m))
+    return out
+
+
+def hq_get_utilisation(h, out):
+    return _get("hq_get_utilisation", h, out)
+
+
+def hq_get_response_pattern(h, out):
+    return _get("hq_get_response_pattern", h, out)
+
+
+def hq_get_workload(h, out):
+    return _get("hq_get_workload", h, out)
+
+
+def hq_get_summary(h) -> np.ndarray:
+    out = np.zeros(5)
+    _check(load().hq_get_summary(h, out.ctypes.data))
+    return out
+
+
+def hq_get_table(h, T=None, masks=None):
+    pt, mt = _ptr(T)
+    pm, mm = _ptr(masks)
+    _check(load().hq_get_table(h, pt, pm, mt if T is not None else mm))
+    return T, masks
+
+
+def hq_get_info(h) -> np.ndarray:
+    out = np.zeros(8, dtype=np.int64)
+    _check(load().hq_get_info(h, out.ctypes.data))
+    return out
+
+
+def hq_profile_sweep(h: int, precision: int, sweeps: int, N: int) -> np.ndarray:
+    out = np.zeros(max(2 * (N - 1), 1), dtype=np.float32)
+    _check(load().hq_profile_sweep(h, precision, sweeps, out.ctypes.data))
+    return out
+
+
+def hq_sweep_bytes(h: int, precision: int) -> float:
+    return float(load().hq_sweep_bytes(h, precision))
+
+
+def hq_destroy(h: int) -> None:
+    if h:
+        load().hq_destroy(h)
+
+
+def hq_launch_count(reset: bool = False) -> int:
+    return int(load().hq_launch_count(1 if reset else 0))
+
+
+# ---- convenience wrapper ---------------------------------------------------------------
+
+class Solver:
+    """Owns one hq_solver handle: create -> load -> solve -> results (host numpy)."""
+
+    def __init__(self, N: int, J: int, mode: int = HQ_LOSS, C: int = 0, stream=None):
+        self.N, self.J, self.mode, self.C = N, J, mode, C
+        self.h = hq_create(N, J, mode, C, stream)
+
+    @classmethod
+    def for_instance(cls, inst, stream=None) -> "Solver":
+        s = cls(inst.N, inst.J, inst.mode, inst.C, stream)
+        s.load(inst.lam_j, inst.nu, inst.pref)
+        return s
+
+    def load(self, lam_j, nu, pref):
+        if isinstance(lam_j, np.ndarray) or not hasattr(lam_j, "is_cuda"):
+            lam_j = np.ascontiguousarray(lam_j, dtype=np.float64)
+            nu = np.ascontiguousarray(nu, dtype=np.float64)
+            pref = np.ascontiguousarray(pref, dtype=np.int32)
+        hq_load(self.h, lam_j, nu, pref)
+
+    def solve(self, tol=1e-10, tol_kind=HQ_TOL_RESIDUAL, precision="fp32+df64", max_sweeps=100000,
+              check_every=8, warm_p=None, fp32_stall=0.0) -> tuple[int, dict]:
+        o = hq_default_opts()
+        o.tol = tol
+        o.tol_kind = tol_kind
+        o.precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
+        o.max_sweeps = max_sweeps
+        o.check_every = check_every
+        o.fp32_stall = fp32_stall
+        keep = None
+        if warm_p is not None:
+            p, m = _ptr(np.ascontiguousarray(warm_p, dtype=np.float64)
+                        if isinstance(warm_p, np.ndarray) else warm_p)
+            keep = warm_p
+            o.warm_start = HQ_WARM_GIVEN
+            o.warm_p = p
+            o.warm_mem = m
+        rc, st = hq_solve(self.h, o)
+        del keep
+        return rc, st.as_dict()
+
+    def stationary(self) -> np.ndarray:
+        return hq_get_stationary(self.h, np.empty(1 << self.N))
+
+    def conditional(self) -> np.ndarray:
+        return hq_get_conditional(self.h, np.empty(1 << self.N))
+
+    def layer_marginals(self) -> tuple[np.ndarray, float]:
+        top = self.N + (self.C if self.mode == HQ_FINITE else 0)
+        pn = np.empty(top + 1)
+        tail = np.zeros(1)
+        hq_get_layer_marginals(self.h, pn, tail)
+        return pn, float(tail[0])
+
+    def utilisation(self) -> np.ndarray:
+        return hq_get_utilisation(self.h, np.empty(self.N))
+
+    def response_pattern(self) -> np.ndarray:
+        return hq_get_response_pattern(self.h, np.empty((self.J, self.N)))
+
+    def workload(self) -> np.ndarray:
+        return hq_get_workload(self.h, np.empty((self.N, self.J)))
+
+    def summary(self) -> dict:
+        s = hq_get_summary(self.h)
+        return {"throughput": s[0], "p_block": s[1], "p_wait": s[2], "residual": s[3],
+                "mean_busy": s[4]}
+
+    def table(self) -> tuple[np.ndarray, np.ndarray]:
+        info = hq_get_info(self.h)
+        T = np.empty(int(info[5]))
+        masks = np.empty(1 << self.N, dtype=np.uint32)
+        hq_get_table(self.h, T, masks)
+        return T, masks
+
+    def close(self):
+        if self.h:
+            hq_destroy(self.h)
+            self.h = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
