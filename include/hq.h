@@ -181,6 +181,26 @@ int hq_profile_sweep(hq_solver* h, int precision, int sweeps, float* ms_out);
  * of p (neighbour layers are L2-resident and not counted).  Host double. */
 double hq_sweep_bytes(const hq_solver* h, int precision);
 
+/* Upward-rate table without any device allocation.  The paper has no
+ * counterpart: this exists for callers that may not allocate device memory
+ * themselves -- code whose every buffer must come from an external pool or a fixed
+ * device-memory budget, or latency-sensitive loops where a cudaMalloc (which can
+ * synchronise the whole device) is not acceptable.
+ *   N: 1..16 units, J: 1..4096 nodes (larger sizes return HQ_EINVAL: the working
+ *      memory is one fixed 4.25 MiB static device array in the library);
+ *   lambda_j (J doubles), pref (J*N int32, rows permutations of 0..N-1): device memory;
+ *   T: device memory for N*2^(N-1) doubles, written in the same pull-form layer-ranked
+ *      layout as hq_get_table;
+ *   stream: a cudaStream_t or NULL.
+ * Calls no cudaMalloc/cudaFree.  The first call on each device looks up the static
+ * array's device address (with that device current); make that first call before
+ * any stream capture.  All calls share the array: calls that overlap on the GPU
+ * race and must be ordered (same stream, or synchronise in between).  Returns after
+ * the work has finished on `stream`; on HQ_EINVAL from a bad row the contents of T
+ * are unspecified. */
+int hq_dispatch_table_static(int N, int J, const double* lambda_j, const int32_t* pref,
+                             double* T, void* stream);
+
 void hq_destroy(hq_solver* h);
 const char* hq_strerror(int code);
 const char* hq_last_error(void);

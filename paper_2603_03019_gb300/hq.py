@@ -76,6 +76,7 @@ _SIGS = {
     "hq_launch_count": (ctypes.c_int64, [_i]),
     "hq_profile_sweep": (_i, [_vp, _i, _i, _vp]),
     "hq_sweep_bytes": (_d, [_vp, _i]),
+    "hq_dispatch_table_static": (_i, [_i, _i, _vp, _vp, _vp, _vp]),
 }
 
 
@@ -210,6 +211,13 @@ def hq_profile_sweep(h: int, precision: int, sweeps: int, N: int) -> np.ndarray:
 
 def hq_sweep_bytes(h: int, precision: int) -> float:
     return float(load().hq_sweep_bytes(h, precision))
+
+
+def hq_dispatch_table_static(N: int, J: int, lambda_j, pref, T, stream=None) -> None:
+    """Upward-rate table without any device allocation (all arguments device tensors)."""
+    s = stream if isinstance(stream, int) or stream is None else stream.cuda_stream
+    _check(load().hq_dispatch_table_static(N, J, lambda_j.data_ptr(), pref.data_ptr(),
+                                           T.data_ptr(), s))
 
 
 def hq_destroy(h: int) -> None:
