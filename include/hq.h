@@ -169,12 +169,18 @@ int hq_get_info(const hq_solver* h, int64_t* out8);
 
 /* Timing of the hot path: run `sweeps` outer iterations (Algorithm 1) of the current
  * iterate in precision `precision` (HQ_PREC_FP64 / HQ_PREC_DF64 / HQ_PREC_FP32;
- * the iterate is converted if needed), kernel by kernel, with CUDA events on the
- * solver's stream around every launch.  ms_out (host, 2*(N-1) floats) receives the
- * mean duration of the gather and update kernels of each layer n = 1..N-1, in
- * order [gather_1, update_1, gather_2, ...].  The iterate advances by `sweeps`
+ * the iterate is converted if needed) as one launch of the persistent sweep kernel,
+ * with CUDA events on the solver's stream around it.  ms_out (host, 1 float)
+ * receives the mean milliseconds per sweep.  The iterate advances by `sweeps`
  * iterations; call hq_solve again for results.  Needs a previous hq_solve. */
 int hq_profile_sweep(hq_solver* h, int precision, int sweeps, float* ms_out);
+
+/* Phase timing of the last launch of the sweep kernel (for profiling): the kernel
+ * runs one phase per layer per sweep plus a closing phase, separated by grid
+ * barriers.  us_out (host, max_out doubles) receives the wall time of each phase in
+ * microseconds, measured on the GPU's global timer; returns the number of phases
+ * written (at most 64 are recorded), or a negative hq_status. */
+int hq_profile_phases(hq_solver* h, double* us_out, int max_out);
 
 /* Algorithmic HBM bytes of one outer iteration in `precision`: per state of
  * layers 1..N-1, its n table entries, r_m, its state mask, one read and one write

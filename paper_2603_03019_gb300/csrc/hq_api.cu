@@ -59,15 +59,33 @@ extern "C" void hq_default_opts(hq_opts* o) {
 
 static void free_all(hq_solver* h) {
   void* ptrs[] = {h->masks, h->RL, h->RH, h->lam_j, h->nu, h->pref, h->pre, h->zeta,
+                  h->b64.rec, h->bdf.rec, h->b32.rec,
                   h->b64.T, h->b64.r, h->b64.p, h->b64.nu, h->bdf.T, h->bdf.r, h->bdf.p, h->bdf.nu,
                   h->b32.T, h->b32.r, h->b32.p, h->b32.nu, h->ab, h->partials, h->sc, h->dflag,
                   h->P, h->pn, h->rho, h->R, h->W, h->summary, h->pcond};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->hsc) cudaFreeHost(h->hsc);
-  for (int i = 0; i < 3; i++)
-    if (h->graph[i]) cudaGraphExecDestroy(h->graph[i]);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+}
+
+// Tile records of one precision (see RecLayout): tiles sized so that a record fits
+// one shared-memory stage of the sweep kernel, a multiple of 32 states.
+static void make_records(hq_solver* h, RecLayout& rl, int esize, int stage_bytes) {
+  memset(&rl, 0, sizeof(rl));
+  rl.esize = esize;
+  for (int n = 0; n <= h->N; n++) {
+    if (n >= 1 && n <= h->N - 1) {
+      const int per = 4 + esize * (n + 1);
+      int tk = stage_bytes / per;
+      if (tk > HQ_MAX_TILE) tk = HQ_MAX_TILE;
+      tk &= ~31;
+      rl.tk[n] = tk;
+      rl.ntiles[n] = (int)((h->lsize[n] + tk - 1) / tk);
+      rl.rbytes[n] = ((int64_t)tk * per + 127) & ~(int64_t)127;
+    }
+    rl.roff[n + 1] = rl.roff[n] + (int64_t)rl.ntiles[n] * rl.rbytes[n];
+  }
 }
 
 template <class T>
@@ -112,7 +130,7 @@ extern "C" int hq_create(int N, int J, int mode, int capacity_C, void* stream, h
   cudaGetDevice(&h->dev);
   h->stream = (cudaStream_t)stream;
   if (!h->stream) {
-    // graphs cannot be captured on the legacy default stream: use a stream of our own
+    // keep the solver's work off the legacy default stream: use a stream of our own
     if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) {
       cudaGetLastError();
       delete h;
@@ -126,20 +144,24 @@ extern "C" int hq_create(int N, int J, int mode, int capacity_C, void* stream, h
   h->toff[0] = 0;
   h->max_layer = 0;
   for (int n = 0; n <= N; n++) {
+    // every layer (and every table row) starts on a 32-entry boundary, so bulk copies
+    // of whole tiles start 16-byte aligned and may read up to 31 entries of padding
     h->lsize[n] = (int64_t)hq_binom(N, n);
-    h->off[n + 1] = h->off[n] + h->lsize[n];
-    h->toff[n + 1] = h->toff[n] + (int64_t)n * h->lsize[n];
-    if (h->lsize[n] > h->max_layer) h->max_layer = h->lsize[n];
+    h->lpad[n] = (h->lsize[n] + 31) & ~(int64_t)31;
+    h->off[n + 1] = h->off[n] + h->lpad[n];
+    h->toff[n + 1] = h->toff[n] + (int64_t)n * h->lpad[n];
+    if (h->lpad[n] > h->max_layer) h->max_layer = h->lpad[n];
   }
   for (int n = N + 2; n < HQ_MAXN + 2; n++) {
     h->off[n] = h->off[N + 1];
     h->toff[n] = h->toff[N + 1];
   }
   h->tentries = h->toff[N + 1];
+  h->Sp = h->off[N + 1];
   h->L = N < HQ_LO_BITS ? N : HQ_LO_BITS;
   h->H = N - h->L;
-  const int64_t S = h->S, TE = h->tentries, half = S / 2 > 0 ? S / 2 : 1;
-  HQ_TRY(dalloc(h, &h->masks, S * 4));
+  const int64_t S = h->S, SP = h->Sp, TE = h->tentries, half = S / 2 > 0 ? S / 2 : 1;
+  HQ_TRY(dalloc(h, &h->masks, SP * 4));
   HQ_TRY(dalloc(h, &h->RL, (int64_t)4 << h->L));
   HQ_TRY(dalloc(h, &h->RH, ((int64_t)4 << h->H) * (h->L + 1)));
   HQ_TRY(dalloc(h, &h->lam_j, (int64_t)J * 8));
@@ -148,18 +170,23 @@ extern "C" int hq_create(int N, int J, int mode, int capacity_C, void* stream, h
   HQ_TRY(dalloc(h, &h->pre, (int64_t)J * N * 4));
   HQ_TRY(dalloc(h, &h->zeta, half * N * 8));
   HQ_TRY(dalloc(h, (double**)&h->b64.T, TE * 8));
-  HQ_TRY(dalloc(h, (float2**)&h->bdf.T, TE * 8));
-  HQ_TRY(dalloc(h, (float**)&h->b32.T, TE * 4));
-  HQ_TRY(dalloc(h, (double**)&h->b64.r, S * 8));
-  HQ_TRY(dalloc(h, (float2**)&h->bdf.r, S * 8));
-  HQ_TRY(dalloc(h, (float**)&h->b32.r, S * 4));
-  HQ_TRY(dalloc(h, (double**)&h->b64.p, S * 8));
-  HQ_TRY(dalloc(h, (float2**)&h->bdf.p, S * 8));
-  HQ_TRY(dalloc(h, (float**)&h->b32.p, S * 4));
+  make_records(h, h->b64.rl, 8, HQ_STAGE_WIDE);
+  make_records(h, h->bdf.rl, 8, HQ_STAGE_WIDE);
+  make_records(h, h->b32.rl, 4, HQ_STAGE_F32);
+  HQ_TRY(dalloc(h, (char**)&h->b64.rec, h->b64.rl.roff[N + 1]));
+  HQ_TRY(dalloc(h, (char**)&h->bdf.rec, h->bdf.rl.roff[N + 1]));
+  HQ_TRY(dalloc(h, (char**)&h->b32.rec, h->b32.rl.roff[N + 1]));
+  HQ_TRY(dalloc(h, (double**)&h->b64.r, SP * 8));
+  HQ_TRY(dalloc(h, (float2**)&h->bdf.r, SP * 8));
+  HQ_TRY(dalloc(h, (float**)&h->b32.r, SP * 4));
+  HQ_TRY(dalloc(h, (double**)&h->b64.p, SP * 8));
+  HQ_TRY(dalloc(h, (float2**)&h->bdf.p, SP * 8));
+  HQ_TRY(dalloc(h, (float**)&h->b32.p, SP * 4));
   HQ_TRY(dalloc(h, (double**)&h->b64.nu, (int64_t)HQ_MAXN * 8));
   HQ_TRY(dalloc(h, (float2**)&h->bdf.nu, (int64_t)HQ_MAXN * 8));
   HQ_TRY(dalloc(h, (float**)&h->b32.nu, (int64_t)HQ_MAXN * 4));
-  HQ_TRY(dalloc(h, (double**)&h->ab, h->max_layer * 16));
+  h->ab_half_bytes = h->max_layer * 16;
+  HQ_TRY(dalloc(h, (double**)&h->ab, 2 * h->ab_half_bytes));
   int64_t blocks = (h->max_layer + HQ_THREADS - 1) / HQ_THREADS;
   h->partials_len = blocks * 2 > 152 * 8 * HQ_MAXN ? blocks * 2 : 152 * 8 * HQ_MAXN;
   HQ_TRY(dalloc(h, &h->partials, h->partials_len * 8));
@@ -180,6 +207,15 @@ extern "C" int hq_create(int N, int J, int mode, int capacity_C, void* stream, h
     return HQ_ENOMEM;
   }
   cudaError_t e = cudaMemsetAsync(h->sc, 0, sizeof(DevScalars), h->stream);
+  {
+    // padding entries are read by whole-tile copies: give them defined (zero) contents
+    void* zero_bufs[] = {h->masks, h->b64.T, h->b64.rec, h->bdf.rec, h->b32.rec, h->b64.r, h->bdf.r,
+                         h->b32.r, h->b64.p, h->bdf.p, h->b32.p};
+    int64_t zero_len[] = {SP * 4, TE * 8, h->b64.rl.roff[N + 1], h->bdf.rl.roff[N + 1],
+                          h->b32.rl.roff[N + 1], SP * 8, SP * 8, SP * 4, SP * 8, SP * 8, SP * 4};
+    for (int i = 0; i < 11 && e == cudaSuccess; i++)
+      e = cudaMemsetAsync(zero_bufs[i], 0, (size_t)zero_len[i], h->stream);
+  }
   if (e != cudaSuccess) {
     int rc = hq_cuda_fail(e, "cudaMemsetAsync", __FILE__, __LINE__);
     free_all(h);
@@ -289,22 +325,21 @@ extern "C" int hq_solve(hq_solver* h, const hq_opts* opts_in, hq_stats* stats) {
   }
   while (!converged && total < o.max_sweeps) {
     const int prec = phases[ph];
-    cudaGraphExec_t g;
-    int nk = 0;
-    rc = hq_get_sweep_graph(h, prec, &g, &nk);
-    if (rc != HQ_OK) return rc;
     int nrun = o.check_every;
     if (nrun > o.max_sweeps - total) nrun = o.max_sweeps - total;
-    for (int i = 0; i < nrun; i++) {
-      HQ_CUDA(cudaGraphLaunch(g, h->stream));
-      hq_count_launch(nk);
-    }
+    rc = hq_run_sweeps(h, prec, nrun, nullptr, nullptr);
+    if (rc != HQ_OK) return rc;
     rc = pull_scalars(h);
     if (rc != HQ_OK) return rc;
     total += nrun;
     sweeps[prec == HQ_PREC_FP32 ? 0 : 1] += nrun;
     checks++;
     step = h->hsc->step;
+    if (h->hsc->flags & 6) {
+      hq_set_error("a bounded wait in the sweep kernel gave up");
+      status = HQ_ETIMEOUT;
+      break;
+    }
     if ((h->hsc->flags & 1) || !isfinite(step)) {
       hq_set_error("non-finite value in the iteration");
       status = HQ_EDIVERGED;
@@ -351,7 +386,7 @@ extern "C" int hq_solve(hq_solver* h, const hq_opts* opts_in, hq_stats* stats) {
     }
     prev_check_step = step;
   }
-  if (status == HQ_EDIVERGED) {
+  if (status == HQ_EDIVERGED || status == HQ_ETIMEOUT) {
     if (stats) {
       memset(stats, 0, sizeof(*stats));
       stats->sweeps_fp32 = sweeps[0];
@@ -446,8 +481,26 @@ extern "C" int hq_get_table(hq_solver* h, double* T, uint32_t* masks, int mem) {
   if (!h) { hq_set_error("NULL solver"); return HQ_EINVAL; }
   if (!h->loaded) { hq_set_error("hq_load has not succeeded"); return HQ_ESTATE; }
   int rc = HQ_OK;
-  if (T) rc = copy_out(h, T, h->b64.T, h->tentries * 8, mem);
-  if (rc == HQ_OK && masks) rc = copy_out(h, masks, h->masks, h->S * 4, mem);
+  // the device layout pads every layer and table row to 32 entries; hand out the
+  // compact layout described in hq.h
+  const cudaMemcpyKind kind = kind_out(mem);
+  int64_t tpos = 0, spos = 0;
+  for (int n = 0; n <= h->N && rc == HQ_OK; n++) {
+    if (T && n >= 1) {
+      cudaError_t e = cudaMemcpy2DAsync((double*)T + tpos, (size_t)h->lsize[n] * 8,
+                                        (const double*)h->b64.T + h->toff[n], (size_t)h->lpad[n] * 8,
+                                        (size_t)h->lsize[n] * 8, (size_t)n, kind, h->stream);
+      if (e != cudaSuccess) rc = hq_cuda_fail(e, "cudaMemcpy2DAsync", __FILE__, __LINE__);
+      tpos += (int64_t)n * h->lsize[n];
+    }
+    if (masks && rc == HQ_OK) {
+      cudaError_t e = cudaMemcpyAsync(masks + spos, h->masks + h->off[n], (size_t)h->lsize[n] * 4,
+                                      kind, h->stream);
+      if (e != cudaSuccess) rc = hq_cuda_fail(e, "cudaMemcpyAsync", __FILE__, __LINE__);
+      spos += h->lsize[n];
+    }
+  }
+  if (rc == HQ_OK) HQ_CUDA(cudaStreamSynchronize(h->stream));
   return rc;
 }
 
@@ -458,7 +511,7 @@ extern "C" int hq_get_info(const hq_solver* h, int64_t* out8) {
   out8[2] = h->mode;
   out8[3] = h->C;
   out8[4] = h->S;
-  out8[5] = h->tentries;
+  out8[5] = (int64_t)h->N << (h->N - 1);
   out8[6] = h->dev_bytes;
   out8[7] = h->max_layer;
   return HQ_OK;
@@ -480,30 +533,42 @@ extern "C" int hq_profile_sweep(hq_solver* h, int precision, int sweeps, float* 
     hq_set_error("precision must be FP64, DF64 or FP32");
     return HQ_EINVAL;
   }
-  const int N = h->N;
-  for (int i = 0; i < 2 * (N - 1); i++) ms_out[i] = 0.f;
-  if (N < 2) return HQ_OK;
+  ms_out[0] = 0.f;
+  if (h->N < 2) return HQ_OK;
   if (h->cur_prec != precision) {
     rc = hq_convert_iterate(h, h->cur_prec, precision);
     if (rc != HQ_OK) return rc;
   }
-  const int nev = 2 * (N - 1) + 1;
-  cudaEvent_t ev[2 * HQ_MAXN + 1];
-  for (int i = 0; i < nev; i++) HQ_CUDA(cudaEventCreate(&ev[i]));
-  for (int s = 0; s < sweeps && rc == HQ_OK; s++) {
-    rc = hq_launch_sweep_timed(h, precision, ev);
-    if (rc != HQ_OK) break;
-    cudaError_t e = cudaEventSynchronize(ev[nev - 1]);
-    if (e != cudaSuccess) { rc = hq_cuda_fail(e, "cudaEventSynchronize", __FILE__, __LINE__); break; }
-    for (int i = 0; i + 1 < nev; i++) {
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, ev[i], ev[i + 1]);
-      ms_out[i] += ms / (float)sweeps;
-    }
-  }
-  for (int i = 0; i < nev; i++) cudaEventDestroy(ev[i]);
+  cudaEvent_t ev0, ev1;
+  HQ_CUDA(cudaEventCreate(&ev0));
+  HQ_CUDA(cudaEventCreate(&ev1));
+  rc = hq_run_sweeps(h, precision, sweeps, ev0, ev1);
   if (rc == HQ_OK) {
-    HQ_CUDA(cudaStreamSynchronize(h->stream));
+    cudaError_t e = cudaEventSynchronize(ev1);
+    if (e != cudaSuccess) rc = hq_cuda_fail(e, "cudaEventSynchronize", __FILE__, __LINE__);
+    float ms = 0.f;
+    if (rc == HQ_OK) cudaEventElapsedTime(&ms, ev0, ev1);
+    ms_out[0] = ms / (float)sweeps;
   }
+  cudaEventDestroy(ev0);
+  cudaEventDestroy(ev1);
   return rc;
+}
+
+extern "C" int hq_profile_phases(hq_solver* h, double* us_out, int max_out) {
+  int rc = need_solved(h);
+  if (rc != HQ_OK) return rc;
+  if (!us_out || max_out < 0) { hq_set_error("us_out NULL"); return HQ_EINVAL; }
+  rc = pull_scalars(h);
+  if (rc != HQ_OK) return rc;
+  const DevScalars* s = h->hsc;
+  int n = 0;
+  unsigned long long prev = s->t_start;
+  for (int g = 0; g < 64 && n < max_out; g++) {
+    const unsigned long long t = s->t_phase[g];
+    if (t <= prev || t == 0) break;
+    us_out[n++] = (double)(t - prev) * 1e-3;
+    prev = t;
+  }
+  return n;
 }

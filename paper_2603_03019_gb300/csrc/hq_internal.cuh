@@ -12,6 +12,21 @@
 #define HQ_MAXN 28
 #define HQ_LO_BITS 12          // low-part width of the split rank tables
 #define HQ_THREADS 256         // threads per CTA of the streaming kernels
+#define HQ_MAX_TILE 448        // states per tile of the sweep (2 x 224 consumer threads)
+#define HQ_STAGE_F32 (20 * 1024)   // tile record bytes, FP32 sweeps
+#define HQ_STAGE_WIDE (21 * 1024)  // tile record bytes, DF64 and FP64 sweeps
+
+// Tile records of one precision: layer n is cut into tiles of tk[n] consecutive
+// states; tile t of layer n is one contiguous record of rbytes[n] bytes at
+// roff[n] + t * rbytes[n]: [tk masks (uint32)] [tk r_m] [n rows of tk table
+// entries], the exact image of the shared-memory stage it is copied into.
+struct RecLayout {
+  int tk[HQ_MAXN + 1];
+  int ntiles[HQ_MAXN + 1];
+  int64_t rbytes[HQ_MAXN + 1];
+  int64_t roff[HQ_MAXN + 2];
+  int esize;
+};
 
 // ---------------------------------------------------------------------------
 // error plumbing (host)
@@ -151,6 +166,8 @@ struct DevScalars {
   int sweeps;                  // sweeps done on the device
   int flags;                   // bit 0: non-finite value seen
   unsigned ticket[4];          // last-block tickets
+  unsigned bar_count;          // grid barrier of the persistent sweep kernel: arrivals
+  unsigned bar_gen;            // grid barrier: generation
   double red[16];              // results of whole-vector reductions
   double lsum[HQ_MAXN + 1];    // sum_m p_n(B_m) per layer (whole-vector pass)
   double lmu[HQ_MAXN + 1];     // sum_m mu_m p_n(B_m) per layer
@@ -158,6 +175,9 @@ struct DevScalars {
   double res_den[HQ_MAXN + 1]; // max_m out_m per layer
   double fac[HQ_MAXN + 1];     // P{B} = fac[w(B)] * p_w(B) after the birth-death step
   double lam;                  // lambda = sum_j lambda_j of the loaded instance
+  double pub[2][8];            // per-phase results published at the persistent kernel's barrier
+  unsigned long long t_start;  // %globaltimer at the start of the last sweep launch (ns)
+  unsigned long long t_phase[64];  // %globaltimer at the release of phase g of that launch
 };
 
 // rank of a state from the split tables (see hq_layout.cu)
@@ -177,7 +197,9 @@ __device__ __forceinline__ float ld_ro(const float* p) { return __ldg(p); }
 
 // per-precision vectors
 struct PrecBufs {
-  void* T = nullptr;   // pull-form table, toff layout
+  RecLayout rl;         // tile records of the sweep kernel
+  void* rec = nullptr;  // tile records (masks, r_m, table rows per tile)
+  void* T = nullptr;   // pull-form table, toff layout (FP64 only: residual, getters)
   void* r = nullptr;   // 1/(lambda + mu_m), layer-ranked
   void* p = nullptr;   // conditional p, layer-ranked
   void* nu = nullptr;  // nu_i in this precision (N)
@@ -189,10 +211,13 @@ struct hq_solver {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   int64_t S = 0;
-  int64_t off[HQ_MAXN + 2];    // layer n states: [off[n], off[n+1])
+  int64_t off[HQ_MAXN + 2];    // layer n states start at off[n] (padded to 32 entries)
   int64_t toff[HQ_MAXN + 2];   // table entries of layer n start at toff[n]
   int64_t lsize[HQ_MAXN + 1];  // C(N, n)
-  int64_t tentries = 0;
+  int64_t lpad[HQ_MAXN + 1];   // C(N, n) rounded up to 32: layer stride, table row stride
+  int64_t Sp = 0;              // padded length of the layer-ranked vectors
+  int64_t tentries = 0;        // padded table length
+  int64_t ab_half_bytes = 0;   // one half of the (A, B) double buffer
   int L = 0, H = 0;            // split rank tables: low L bits, high H bits
   int64_t max_layer = 0;
   int64_t dev_bytes = 0;
@@ -211,7 +236,7 @@ struct hq_solver {
   uint32_t* pre = nullptr;     // J x N: units ranked before u by node j
   double* zeta = nullptr;      // N x 2^(N-1) scratch of the subset-sum transforms
   PrecBufs b64, bdf, b32;
-  void* ab = nullptr;          // per-layer (A, B) scratch, max_layer x 2 x 8 bytes
+  void* ab = nullptr;          // (A, B) pairs of two consecutive layers (double buffer)
   double* partials = nullptr;  // block partials of the reductions
   int64_t partials_len = 0;
   DevScalars* sc = nullptr;
@@ -225,9 +250,6 @@ struct hq_solver {
   double* W = nullptr;         // N x J
   double* summary = nullptr;   // 8
   double* pcond = nullptr;     // S, y-order conditional (normalised)
-  // sweep graphs per precision
-  cudaGraphExec_t graph[3] = {nullptr, nullptr, nullptr};
-  int graph_kernels[3] = {0, 0, 0};
   double ms_table = 0;
 };
 
@@ -248,9 +270,7 @@ int hq_zeta_subset(hq_solver* h, double* buf, int bits, int count, bool superset
 // sweep (hq_sweep.cu)
 int hq_init_iterate(hq_solver* h, int prec, const double* warm_y, int warm_mem);
 int hq_convert_iterate(hq_solver* h, int from, int to);
-int hq_launch_sweep(hq_solver* h, int prec);
-int hq_launch_sweep_timed(hq_solver* h, int prec, cudaEvent_t* ev);
-int hq_get_sweep_graph(hq_solver* h, int prec, cudaGraphExec_t* out, int* kernels);
+int hq_run_sweeps(hq_solver* h, int prec, int nsweeps, cudaEvent_t ev0, cudaEvent_t ev1);
 PrecBufs& hq_bufs(hq_solver* h, int prec);
 
 // results (hq_post.cu)

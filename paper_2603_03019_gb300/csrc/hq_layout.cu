@@ -37,10 +37,11 @@ static BinomTable make_binom_table() {
 
 struct LayoutArgs {
   int N;
-  int64_t off[HQ_MAXN + 2];
+  int64_t off[HQ_MAXN + 2];    // padded layer starts
+  int64_t lsize[HQ_MAXN + 1];
 };
 
-// colex unrank: state mask of global layer-ranked index g
+// colex unrank: state mask of global layer-ranked index g (padding slots get 0)
 __global__ void k_masks(LayoutArgs a, BinomTable bt, uint32_t* masks, int64_t S) {
   __shared__ uint32_t sb[33][33];
   for (int i = threadIdx.x; i < 33 * 33; i += blockDim.x) sb[i / 33][i % 33] = bt.c[i / 33][i % 33];
@@ -49,6 +50,10 @@ __global__ void k_masks(LayoutArgs a, BinomTable bt, uint32_t* masks, int64_t S)
   if (g >= S) return;
   int n = 0;
   while (n < a.N && a.off[n + 1] <= g) n++;
+  if (g - a.off[n] >= a.lsize[n]) {
+    masks[g] = 0u;
+    return;
+  }
   uint32_t k = (uint32_t)(g - a.off[n]);
   uint32_t x = 0;
   int c = a.N - 1;
@@ -98,7 +103,8 @@ int hq_build_layout(hq_solver* h) {
   LayoutArgs a;
   a.N = N;
   for (int i = 0; i < HQ_MAXN + 2; i++) a.off[i] = h->off[i];
-  int64_t S = h->S;
+  for (int i = 0; i <= HQ_MAXN; i++) a.lsize[i] = i <= N ? h->lsize[i] : 0;
+  int64_t S = h->Sp;
   k_masks<<<(unsigned)((S + 255) / 256), 256, 0, h->stream>>>(a, bt, h->masks, S);
   HQ_LAUNCHED();
   k_rank_lo<<<(unsigned)(((1u << h->L) + 255) / 256), 256, 0, h->stream>>>(h->L, bt, h->RL);
@@ -171,21 +177,44 @@ int hq_validate_device(hq_solver* h) {
 // r_m = 1 / (lambda_m + mu_m), layer-ranked, in the three precisions.
 // lambda_m = lambda except the all-busy state of the loss system (0).
 // ---------------------------------------------------------------------------
-__global__ void k_rates(int N, int64_t S, const uint32_t* masks, const double* nu, double lam,
-                        double lam_full, double* r64, float2* rdf, float* r32) {
+struct RateRecords {
+  RecLayout rl[3];  // FP64, DF64, FP32 tile records of the sweep
+  unsigned char* rec[3];
+};
+
+__global__ void k_rates(LayoutArgs la, int64_t S, const uint32_t* masks, const double* nu, double lam,
+                        double lam_full, double* r64, float2* rdf, float* r32, RateRecords rr) {
+  const int N = la.N;
   __shared__ double snu[HQ_MAXN];
   if (threadIdx.x < N) snu[threadIdx.x] = nu[threadIdx.x];
   __syncthreads();
   int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= S) return;
+  int n = 0;
+  while (n < N && la.off[n + 1] <= g) n++;
+  if (g - la.off[n] >= la.lsize[n]) return;  // padding keeps its zeros
   uint32_t x = masks[g];
   double mu = 0.0;
   for (uint32_t y = x; y; y &= y - 1) mu += snu[__ffs(y) - 1];
-  double lm = (x == (uint32_t)(S - 1)) ? lam_full : lam;
+  double lm = (n == N) ? lam_full : lam;
   double r = 1.0 / (lm + mu);
   r64[g] = r;
   rdf[g] = df_from_double(r);
   r32[g] = (float)r;
+  if (n >= 1 && n <= N - 1) {
+    // r_m inside the tile records of the sweep: after the tk masks of the tile
+    const int64_t k = g - la.off[n];
+    for (int q = 0; q < 3; q++) {
+      const RecLayout& rl = rr.rl[q];
+      const int tk = rl.tk[n];
+      const int64_t t = k / tk;
+      const int j = (int)(k - t * tk);
+      unsigned char* base = rr.rec[q] + rl.roff[n] + t * rl.rbytes[n] + (int64_t)tk * 4;
+      if (q == 0) ((double*)base)[j] = r;
+      else if (q == 1) ((float2*)base)[j] = df_from_double(r);
+      else ((float*)base)[j] = (float)r;
+    }
+  }
 }
 
 __global__ void k_nu_prec(int N, const double* nu, float2* nudf, float* nu32) {
@@ -198,9 +227,20 @@ __global__ void k_nu_prec(int N, const double* nu, float2* nudf, float* nu32) {
 
 int hq_build_rates(hq_solver* h) {
   double lam_full = h->mode == HQ_LOSS ? 0.0 : h->lam;
-  k_rates<<<(unsigned)((h->S + 255) / 256), 256, 0, h->stream>>>(
-      h->N, h->S, h->masks, h->nu, h->lam, lam_full, (double*)h->b64.r, (float2*)h->bdf.r,
-      (float*)h->b32.r);
+  LayoutArgs la;
+  la.N = h->N;
+  for (int i = 0; i < HQ_MAXN + 2; i++) la.off[i] = h->off[i];
+  for (int i = 0; i <= HQ_MAXN; i++) la.lsize[i] = i <= h->N ? h->lsize[i] : 0;
+  RateRecords rr;
+  rr.rl[0] = h->b64.rl;
+  rr.rl[1] = h->bdf.rl;
+  rr.rl[2] = h->b32.rl;
+  rr.rec[0] = (unsigned char*)h->b64.rec;
+  rr.rec[1] = (unsigned char*)h->bdf.rec;
+  rr.rec[2] = (unsigned char*)h->b32.rec;
+  k_rates<<<(unsigned)((h->Sp + 255) / 256), 256, 0, h->stream>>>(
+      la, h->Sp, h->masks, h->nu, h->lam, lam_full, (double*)h->b64.r, (float2*)h->bdf.r,
+      (float*)h->b32.r, rr);
   HQ_LAUNCHED();
   HQ_CUDA(cudaMemcpyAsync(h->b64.nu, h->nu, sizeof(double) * h->N, cudaMemcpyDeviceToDevice,
                           h->stream));

@@ -156,6 +156,7 @@ __global__ void k_birth_death(DevScalars* sc, int N, int mode, int C, double lam
 struct ResArgs {
   int N, L, n, mode;
   int64_t Ln;
+  int64_t Lp;              // table row stride of layer n
   const uint32_t* masks;   // layer n
   const uint32_t* RL;
   const uint32_t* RH;
@@ -200,7 +201,7 @@ __global__ void __launch_bounds__(256) k_residual(ResArgs a) {
       mu += snu[b];
       uint32_t rk = (b < L) ? s_RL[lo ^ (1u << b)] + __ldg(rh + w - 1)
                             : rl + __ldg(a.RH + (size_t)(hi ^ (1u << (b - L))) * (L + 1) + w);
-      up = fma(__ldg(a.p_dn + rk), __ldcs(a.T + (int64_t)s_ * a.Ln + k), up);
+      up = fma(__ldg(a.p_dn + rk), __ldcs(a.T + (int64_t)s_ * a.Lp + k), up);
     }
     if (n < a.N) {
       uint32_t full = (1u << a.N) - 1u;
@@ -245,7 +246,8 @@ __global__ void k_residual_final(DevScalars* sc, int N, double* summary) {
 
 struct ScatterArgs {
   int N;
-  int64_t off[HQ_MAXN + 2];
+  int64_t off[HQ_MAXN + 2];  // padded layer starts
+  int64_t lsize[HQ_MAXN + 1];
 };
 
 // P{B} in y-order and the normalised conditional p_n(B) in y-order
@@ -255,6 +257,7 @@ __global__ void k_scatter(ScatterArgs a, int64_t S, const uint32_t* masks, const
   if (g >= S) return;
   int n = 0;
   while (n < a.N && a.off[n + 1] <= g) n++;
+  if (g - a.off[n] >= a.lsize[n]) return;  // padding
   uint32_t x = masks[g];
   double v = p[g];
   P[x] = sc->fac[n] * v;
@@ -407,6 +410,7 @@ static int residual_pass(hq_solver* h) {
     a.n = n;
     a.mode = h->mode;
     a.Ln = h->lsize[n];
+    a.Lp = h->lpad[n];
     a.masks = h->masks + h->off[n];
     a.RL = h->RL;
     a.RH = h->RH;
@@ -449,8 +453,9 @@ int hq_finalize(hq_solver* h, int prec, bool full_outputs, double* residual_out)
     ScatterArgs sa;
     sa.N = h->N;
     for (int i = 0; i < HQ_MAXN + 2; i++) sa.off[i] = h->off[i];
-    unsigned grid = (unsigned)((h->S + 255) / 256);
-    k_scatter<<<grid, 256, 0, h->stream>>>(sa, h->S, h->masks, (const double*)h->b64.p, h->sc, h->P,
+    for (int i = 0; i <= HQ_MAXN; i++) sa.lsize[i] = i <= h->N ? h->lsize[i] : 0;
+    unsigned grid = (unsigned)((h->Sp + 255) / 256);
+    k_scatter<<<grid, 256, 0, h->stream>>>(sa, h->Sp, h->masks, (const double*)h->b64.p, h->sc, h->P,
                                            h->pcond);
     HQ_LAUNCHED();
     int64_t want = (h->S + 255) / 256;

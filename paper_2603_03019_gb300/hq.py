@@ -77,6 +77,7 @@ _SIGS = {
     "hq_profile_sweep": (_i, [_vp, _i, _i, _vp]),
     "hq_sweep_bytes": (_d, [_vp, _i]),
     "hq_dispatch_table_static": (_i, [_i, _i, _vp, _vp, _vp, _vp]),
+    "hq_profile_phases": (_i, [_vp, _vp, _i]),
 }
 
 
@@ -203,10 +204,19 @@ def hq_get_info(h) -> np.ndarray:
     return out
 
 
-def hq_profile_sweep(h: int, precision: int, sweeps: int, N: int) -> np.ndarray:
-    out = np.zeros(max(2 * (N - 1), 1), dtype=np.float32)
+def hq_profile_sweep(h: int, precision: int, sweeps: int) -> float:
+    """Mean milliseconds per sweep of one persistent-kernel launch of `sweeps` sweeps."""
+    out = np.zeros(1, dtype=np.float32)
     _check(load().hq_profile_sweep(h, precision, sweeps, out.ctypes.data))
-    return out
+    return float(out[0])
+
+
+def hq_profile_phases(h: int, max_out: int = 64) -> np.ndarray:
+    """Per-phase wall time (us) of the last sweep-kernel launch."""
+    out = np.zeros(max_out)
+    n = load().hq_profile_phases(h, out.ctypes.data, max_out)
+    _check(n if n < 0 else 0)
+    return out[:n]
 
 
 def hq_sweep_bytes(h: int, precision: int) -> float:
