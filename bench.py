@@ -38,10 +38,11 @@ from paper_2603_03019_gb300 import instances as I  # noqa: E402
 WORKLOADS = {
     "n24": lambda seed: I.large_infinite_n24(seed),
     "n23": lambda seed: I.large_infinite_n24(seed, N=23),
+    "n22": lambda seed: I.large_infinite_n24(seed, N=22),
     "n20": lambda seed: I.mixed_n20(seed, 0.6),
     "n10": lambda seed: I.small_loss_n10(seed),
 }
-BASE_SEED = {"n24": 3001, "n23": 3001, "n20": 2001, "n10": 1001}
+BASE_SEED = {"n24": 3001, "n23": 3001, "n22": 3001, "n20": 2001, "n10": 1001}
 
 
 def parse():
@@ -75,7 +76,8 @@ def run_profile(args):
     s.load(torch.tensor(inst.lam_j, device=dev), torch.tensor(inst.nu, device=dev),
            torch.tensor(inst.pref, device=dev))
     torch.cuda.synchronize()
-    rc, st = s.solve(tol=0.0, tol_kind=hq.HQ_TOL_STEP, precision="df64", max_sweeps=args.sweeps,
+    prec = args.precision if args.precision in ("fp32", "df64", "fp64") else "df64"
+    rc, st = s.solve(tol=0.0, tol_kind=hq.HQ_TOL_STEP, precision=prec, max_sweeps=args.sweeps,
                      check_every=args.sweeps)
     s.close()
     print(json.dumps({"profile": inst.name, "sweeps": st["sweeps_hi"], "rc": rc}))

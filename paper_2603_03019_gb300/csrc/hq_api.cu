@@ -59,7 +59,7 @@ extern "C" void hq_default_opts(hq_opts* o) {
 
 static void free_all(hq_solver* h) {
   void* ptrs[] = {h->masks, h->RL, h->RH, h->lam_j, h->nu, h->pref, h->pre, h->zeta,
-                  h->b64.rec, h->bdf.rec, h->b32.rec,
+                  h->lidx, h->items,
                   h->b64.T, h->b64.r, h->b64.p, h->b64.nu, h->bdf.T, h->bdf.r, h->bdf.p, h->bdf.nu,
                   h->b32.T, h->b32.r, h->b32.p, h->b32.nu, h->ab, h->partials, h->sc, h->dflag,
                   h->P, h->pn, h->rho, h->R, h->W, h->summary, h->pcond};
@@ -67,25 +67,6 @@ static void free_all(hq_solver* h) {
     if (p) cudaFree(p);
   if (h->hsc) cudaFreeHost(h->hsc);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
-}
-
-// Tile records of one precision (see RecLayout): tiles sized so that a record fits
-// one shared-memory stage of the sweep kernel, a multiple of 32 states.
-static void make_records(hq_solver* h, RecLayout& rl, int esize, int stage_bytes) {
-  memset(&rl, 0, sizeof(rl));
-  rl.esize = esize;
-  for (int n = 0; n <= h->N; n++) {
-    if (n >= 1 && n <= h->N - 1) {
-      const int per = 4 + esize * (n + 1);
-      int tk = stage_bytes / per;
-      if (tk > HQ_MAX_TILE) tk = HQ_MAX_TILE;
-      tk &= ~31;
-      rl.tk[n] = tk;
-      rl.ntiles[n] = (int)((h->lsize[n] + tk - 1) / tk);
-      rl.rbytes[n] = ((int64_t)tk * per + 127) & ~(int64_t)127;
-    }
-    rl.roff[n + 1] = rl.roff[n] + (int64_t)rl.ntiles[n] * rl.rbytes[n];
-  }
 }
 
 template <class T>
@@ -170,12 +151,9 @@ extern "C" int hq_create(int N, int J, int mode, int capacity_C, void* stream, h
   HQ_TRY(dalloc(h, &h->pre, (int64_t)J * N * 4));
   HQ_TRY(dalloc(h, &h->zeta, half * N * 8));
   HQ_TRY(dalloc(h, (double**)&h->b64.T, TE * 8));
-  make_records(h, h->b64.rl, 8, HQ_STAGE_WIDE);
-  make_records(h, h->bdf.rl, 8, HQ_STAGE_WIDE);
-  make_records(h, h->b32.rl, 4, HQ_STAGE_F32);
-  HQ_TRY(dalloc(h, (char**)&h->b64.rec, h->b64.rl.roff[N + 1]));
-  HQ_TRY(dalloc(h, (char**)&h->bdf.rec, h->bdf.rl.roff[N + 1]));
-  HQ_TRY(dalloc(h, (char**)&h->b32.rec, h->b32.rl.roff[N + 1]));
+  HQ_TRY(dalloc(h, (float2**)&h->bdf.T, TE * 8));
+  HQ_TRY(dalloc(h, (float**)&h->b32.T, TE * 4));
+  HQ_TRY(dalloc(h, &h->lidx, SP * 12));
   HQ_TRY(dalloc(h, (double**)&h->b64.r, SP * 8));
   HQ_TRY(dalloc(h, (float2**)&h->bdf.r, SP * 8));
   HQ_TRY(dalloc(h, (float**)&h->b32.r, SP * 4));
@@ -185,7 +163,8 @@ extern "C" int hq_create(int N, int J, int mode, int capacity_C, void* stream, h
   HQ_TRY(dalloc(h, (double**)&h->b64.nu, (int64_t)HQ_MAXN * 8));
   HQ_TRY(dalloc(h, (float2**)&h->bdf.nu, (int64_t)HQ_MAXN * 8));
   HQ_TRY(dalloc(h, (float**)&h->b32.nu, (int64_t)HQ_MAXN * 4));
-  h->ab_half_bytes = h->max_layer * 16;
+  // the staging copies of the sweep read up to 15 bytes past a layer's last pair
+  h->ab_half_bytes = h->max_layer * 16 + 256;
   HQ_TRY(dalloc(h, (double**)&h->ab, 2 * h->ab_half_bytes));
   int64_t blocks = (h->max_layer + HQ_THREADS - 1) / HQ_THREADS;
   h->partials_len = blocks * 2 > 152 * 8 * HQ_MAXN ? blocks * 2 : 152 * 8 * HQ_MAXN;
@@ -208,12 +187,12 @@ extern "C" int hq_create(int N, int J, int mode, int capacity_C, void* stream, h
   }
   cudaError_t e = cudaMemsetAsync(h->sc, 0, sizeof(DevScalars), h->stream);
   {
-    // padding entries are read by whole-tile copies: give them defined (zero) contents
-    void* zero_bufs[] = {h->masks, h->b64.T, h->b64.rec, h->bdf.rec, h->b32.rec, h->b64.r, h->bdf.r,
-                         h->b32.r, h->b64.p, h->bdf.p, h->b32.p};
-    int64_t zero_len[] = {SP * 4, TE * 8, h->b64.rl.roff[N + 1], h->bdf.rl.roff[N + 1],
-                          h->b32.rl.roff[N + 1], SP * 8, SP * 8, SP * 4, SP * 8, SP * 8, SP * 4};
-    for (int i = 0; i < 11 && e == cudaSuccess; i++)
+    // padding entries are read by the bulk copies: give them defined (zero) contents
+    void* zero_bufs[] = {h->masks, h->b64.T, h->b64.r, h->bdf.r, h->b32.r, h->b64.p, h->bdf.p,
+                         h->b32.p, h->ab};
+    int64_t zero_len[] = {SP * 4, TE * 8, SP * 8, SP * 8, SP * 4, SP * 8, SP * 8, SP * 4,
+                          2 * h->ab_half_bytes};
+    for (int i = 0; i < 9 && e == cudaSuccess; i++)
       e = cudaMemsetAsync(zero_bufs[i], 0, (size_t)zero_len[i], h->stream);
   }
   if (e != cudaSuccess) {
@@ -223,6 +202,7 @@ extern "C" int hq_create(int N, int J, int mode, int capacity_C, void* stream, h
     return rc;
   }
   HQ_TRY(hq_build_layout(h));
+  HQ_TRY(hq_build_items(h));
   e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) {
     int rc = hq_cuda_fail(e, "layout build", __FILE__, __LINE__);
@@ -269,6 +249,8 @@ extern "C" int hq_load(hq_solver* h, const double* lambda_j, const double* nu, c
   rc = hq_build_table(h);
   if (rc != HQ_OK) return rc;
   rc = hq_build_rates(h);
+  if (rc != HQ_OK) return rc;
+  rc = hq_convert_tables(h);
   if (rc != HQ_OK) return rc;
   HQ_CUDA(cudaStreamSynchronize(h->stream));
   h->ms_table = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();

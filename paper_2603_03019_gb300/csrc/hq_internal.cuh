@@ -10,23 +10,20 @@
 #include "../../include/hq.h"
 
 #define HQ_MAXN 28
-#define HQ_LO_BITS 12          // low-part width of the split rank tables
+#define HQ_LO_BITS 10          // low-part width of the split rank tables
 #define HQ_THREADS 256         // threads per CTA of the streaming kernels
-#define HQ_MAX_TILE 448        // states per tile of the sweep (2 x 224 consumer threads)
-#define HQ_STAGE_F32 (20 * 1024)   // tile record bytes, FP32 sweeps
-#define HQ_STAGE_WIDE (21 * 1024)  // tile record bytes, DF64 and FP64 sweeps
 
-// Tile records of one precision: layer n is cut into tiles of tk[n] consecutive
-// states; tile t of layer n is one contiguous record of rbytes[n] bytes at
-// roff[n] + t * rbytes[n]: [tk masks (uint32)] [tk r_m] [n rows of tk table
-// entries], the exact image of the shared-memory stage it is copied into.
-struct RecLayout {
-  int tk[HQ_MAXN + 1];
-  int ntiles[HQ_MAXN + 1];
-  int64_t rbytes[HQ_MAXN + 1];
-  int64_t roff[HQ_MAXN + 2];
-  int esize;
-};
+// Work items of the sweep.  A rank block (hi, w) of layer n is the set of its states whose
+// high part (bits >= L) is hi and whose low part has w busy units; it holds C(L, w)
+// states at the consecutive ranks RH[hi][w] + RL[lo].  The low-part neighbours of its
+// states are the whole blocks (hi, w-1) of layer n-1 and (hi, w+1) of layer n+1 (at most
+// C(10, 5) = 252 states each); a high-part neighbour across unit L+j sits at rank
+// RH[hi ^ 2^j][w] + RL[lo] of layer n -/+ 1, so consecutive states of a block have their
+// high-part neighbours at consecutive ranks.  An item is a run of at most 32 consecutive
+// states of one block, processed by one warp: uint4 {rank0, hi | w << 20 | (count-1) << 24,
+// rank of block (hi, w-1) in layer n-1, rank of block (hi, w+1) in layer n+1}.
+#define HQ_ITEM_HI_BITS 20
+#define HQ_MAX_BLOCK 252   // C(HQ_LO_BITS, HQ_LO_BITS / 2)
 
 // ---------------------------------------------------------------------------
 // error plumbing (host)
@@ -114,7 +111,7 @@ struct PolF64 {
   __device__ static T norm(T a) { return a; }
   __device__ static T from_d(double x) { return x; }
   __device__ static double to_d(T a) { return a; }
-  __device__ static double absdiff(T a, T b) { return fabs(a - b); }
+  __device__ static float absdiff(T a, T b) { return (float)fabs(a - b); }
   __device__ static T shfl_xor(T a, int m) { return __shfl_xor_sync(0xffffffffu, a, m); }
 };
 struct PolDF {
@@ -129,8 +126,8 @@ struct PolDF {
   __device__ static T from_d(double x) { return df_from_double(x); }
   __device__ static double to_d(T a) { return df_to_double(a); }
   // |a - b| for nearby values: the hi difference is exact (Sterbenz), lo adds the rest
-  __device__ static double absdiff(T a, T b) {
-    return (double)fabsf(__fadd_rn(__fsub_rn(a.x, b.x), __fsub_rn(a.y, b.y)));
+  __device__ static float absdiff(T a, T b) {
+    return fabsf(__fadd_rn(__fsub_rn(a.x, b.x), __fsub_rn(a.y, b.y)));
   }
   __device__ static T shfl_xor(T a, int m) {
     return make_float2(__shfl_xor_sync(0xffffffffu, a.x, m), __shfl_xor_sync(0xffffffffu, a.y, m));
@@ -147,7 +144,7 @@ struct PolF32 {
   __device__ static T norm(T a) { return a; }
   __device__ static T from_d(double x) { return (float)x; }
   __device__ static double to_d(T a) { return (double)a; }
-  __device__ static double absdiff(T a, T b) { return (double)fabsf(a - b); }
+  __device__ static float absdiff(T a, T b) { return fabsf(a - b); }
   __device__ static T shfl_xor(T a, int m) { return __shfl_xor_sync(0xffffffffu, a, m); }
 };
 
@@ -197,9 +194,7 @@ __device__ __forceinline__ float ld_ro(const float* p) { return __ldg(p); }
 
 // per-precision vectors
 struct PrecBufs {
-  RecLayout rl;         // tile records of the sweep kernel
-  void* rec = nullptr;  // tile records (masks, r_m, table rows per tile)
-  void* T = nullptr;   // pull-form table, toff layout (FP64 only: residual, getters)
+  void* T = nullptr;   // pull-form table in this precision, toff layout
   void* r = nullptr;   // 1/(lambda + mu_m), layer-ranked
   void* p = nullptr;   // conditional p, layer-ranked
   void* nu = nullptr;  // nu_i in this precision (N)
@@ -229,6 +224,9 @@ struct hq_solver {
   uint32_t* masks = nullptr;   // S, layer-ranked state masks
   uint32_t* RL = nullptr;      // 2^L
   uint32_t* RH = nullptr;      // 2^H x (L+1)
+  uint32_t* lidx = nullptr;    // 3 x Sp: low-part neighbour positions (4 bytes a word)
+  uint4* items = nullptr;      // work items of the sweep, layer by layer
+  int ifirst[HQ_MAXN + 2];     // items of layer n: [ifirst[n], ifirst[n+1])
   // instance
   double* lam_j = nullptr;     // J
   double* nu = nullptr;        // N
@@ -262,6 +260,10 @@ double hq_binom(int n, int k);
 int hq_build_layout(hq_solver* h);
 int hq_validate_device(hq_solver* h);
 int hq_build_rates(hq_solver* h);  // r_m in all precisions
+
+// work items and low-part positions of the sweep (hq_items.cu)
+int hq_build_items(hq_solver* h);     // at hq_create, after the layout
+int hq_convert_tables(hq_solver* h);  // at hq_load: FP32 and DF64 copies of the table
 
 // table (hq_table.cu)
 int hq_build_table(hq_solver* h);

@@ -1,0 +1,126 @@
+// Work items of the sweep kernel (built on the host from N alone, at hq_create), the
+// positions of each state's low-part neighbours inside their rank blocks (device, at
+// hq_create), and the FP32 / DF64 copies of the pull-form table (device, at hq_load).
+// The item format is described with HQ_ITEM_HI_BITS in hq_internal.cuh.
+#include <vector>
+
+#include "hq_internal.cuh"
+
+namespace {
+
+struct HostBinom {
+  uint64_t c[33][33];
+  HostBinom() {
+    for (int n = 0; n <= 32; n++)
+      for (int k = 0; k <= 32; k++) c[n][k] = k > n ? 0 : (uint64_t)hq_binom(n, k);
+  }
+};
+
+// rank of the first state of block (hi, w): the high-part term of the split rank
+uint64_t rank_hi(const HostBinom& B, int L, uint32_t hi, int w) {
+  uint64_t r = 0;
+  int k = 0;
+  for (int b = 0; hi >> b; b++)
+    if ((hi >> b) & 1u) {
+      const int idx = w + k + 1;
+      r += idx <= 32 ? B.c[L + b][idx] : 0;
+      k++;
+    }
+  return r;
+}
+
+// Word q of state g holds bytes 4q..4q+3 of its low-part neighbour positions: byte k < w
+// is RL[lo ^ 2^u] for the k-th busy unit u of lo (increasing), then byte w + k is
+// RL[lo | 2^u] for the k-th idle unit u < L of lo (increasing).  RL[.] is the position of
+// a state inside its rank block, so these index the staged blocks (hi, w -/+ 1).
+__global__ void k_lidx(int L, int64_t Sp, const uint32_t* masks, const uint32_t* RL, uint32_t* lidx) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= Sp) return;
+  const uint32_t lo = masks[g] & ((1u << L) - 1u);
+  uint32_t wd[3] = {0u, 0u, 0u};
+  int k = 0;
+  for (int u = 0; u < L; u++)
+    if ((lo >> u) & 1u) {
+      wd[k >> 2] |= (RL[lo ^ (1u << u)] & 0xffu) << (8 * (k & 3));
+      k++;
+    }
+  for (int u = 0; u < L; u++)
+    if (!((lo >> u) & 1u)) {
+      wd[k >> 2] |= (RL[lo | (1u << u)] & 0xffu) << (8 * (k & 3));
+      k++;
+    }
+  for (int q = 0; q < 3; q++) lidx[(int64_t)q * Sp + g] = wd[q];
+}
+
+__global__ void k_table_conv(int64_t n, const double* T64, float* T32, float2* Tdf) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double v = T64[i];
+  T32[i] = (float)v;
+  Tdf[i] = df_from_double(v);
+}
+
+}  // namespace
+
+int hq_build_items(hq_solver* h) {
+  static const HostBinom B;
+  const int N = h->N, L = h->L, H = h->H;
+  if (H > HQ_ITEM_HI_BITS) {
+    hq_set_error("item builder: high part too wide");
+    return HQ_EINVAL;
+  }
+  std::vector<uint4> items;
+  for (int n = 0; n <= N; n++) {
+    h->ifirst[n] = (int)items.size();
+    if (n < 1 || n > N - 1) continue;
+    uint64_t expect = 0;  // blocks come in increasing rank order, without gaps
+    for (uint32_t hi = 0; hi < (1u << H); hi++) {
+      const int w = n - __builtin_popcount(hi);
+      if (w < 0 || w > L) continue;
+      const uint64_t start = rank_hi(B, L, hi, w);
+      const int size = (int)B.c[L][w];
+      if (start != expect) {
+        hq_set_error("item builder: rank blocks out of order");
+        return HQ_ECUDA;
+      }
+      expect = start + (uint64_t)size;
+      // layer 0 is the empty state (p_0 = 1, no (A, B) pairs): no block below layer 1
+      const uint32_t dn = (w >= 1 && n >= 2) ? (uint32_t)rank_hi(B, L, hi, w - 1) : 0u;
+      const uint32_t up = w < L ? (uint32_t)rank_hi(B, L, hi, w + 1) : 0u;
+      for (int s0 = 0; s0 < size; s0 += 32) {
+        const int c = size - s0 < 32 ? size - s0 : 32;
+        items.push_back(make_uint4((uint32_t)(start + s0),
+                                   hi | ((uint32_t)w << HQ_ITEM_HI_BITS) | ((uint32_t)(c - 1) << 24), dn, up));
+      }
+    }
+    if (expect != (uint64_t)h->lsize[n]) {
+      hq_set_error("item builder: rank blocks do not cover the layer");
+      return HQ_ECUDA;
+    }
+  }
+  h->ifirst[N + 1] = (int)items.size();
+  for (int n = N + 2; n < HQ_MAXN + 2; n++) h->ifirst[n] = h->ifirst[N + 1];
+  const size_t bytes = sizeof(uint4) * (items.empty() ? 1 : items.size());
+  cudaError_t e = cudaMalloc((void**)&h->items, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    hq_set_error("cudaMalloc of the sweep items failed");
+    return HQ_ENOMEM;
+  }
+  h->dev_bytes += (int64_t)bytes;
+  if (!items.empty())
+    HQ_CUDA(cudaMemcpyAsync(h->items, items.data(), bytes, cudaMemcpyHostToDevice, h->stream));
+  HQ_CUDA(cudaStreamSynchronize(h->stream));  // the host vector goes out of scope
+  k_lidx<<<(unsigned)((h->Sp + 255) / 256), 256, 0, h->stream>>>(h->L, h->Sp, h->masks, h->RL, h->lidx);
+  HQ_LAUNCHED();
+  return HQ_OK;
+}
+
+int hq_convert_tables(hq_solver* h) {
+  const int64_t n = h->tentries;
+  if (n == 0) return HQ_OK;
+  k_table_conv<<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(n, (const double*)h->b64.T,
+                                                                    (float*)h->b32.T, (float2*)h->bdf.T);
+  HQ_LAUNCHED();
+  return HQ_OK;
+}

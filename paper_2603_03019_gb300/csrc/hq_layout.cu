@@ -177,13 +177,8 @@ int hq_validate_device(hq_solver* h) {
 // r_m = 1 / (lambda_m + mu_m), layer-ranked, in the three precisions.
 // lambda_m = lambda except the all-busy state of the loss system (0).
 // ---------------------------------------------------------------------------
-struct RateRecords {
-  RecLayout rl[3];  // FP64, DF64, FP32 tile records of the sweep
-  unsigned char* rec[3];
-};
-
 __global__ void k_rates(LayoutArgs la, int64_t S, const uint32_t* masks, const double* nu, double lam,
-                        double lam_full, double* r64, float2* rdf, float* r32, RateRecords rr) {
+                        double lam_full, double* r64, float2* rdf, float* r32) {
   const int N = la.N;
   __shared__ double snu[HQ_MAXN];
   if (threadIdx.x < N) snu[threadIdx.x] = nu[threadIdx.x];
@@ -201,20 +196,6 @@ __global__ void k_rates(LayoutArgs la, int64_t S, const uint32_t* masks, const d
   r64[g] = r;
   rdf[g] = df_from_double(r);
   r32[g] = (float)r;
-  if (n >= 1 && n <= N - 1) {
-    // r_m inside the tile records of the sweep: after the tk masks of the tile
-    const int64_t k = g - la.off[n];
-    for (int q = 0; q < 3; q++) {
-      const RecLayout& rl = rr.rl[q];
-      const int tk = rl.tk[n];
-      const int64_t t = k / tk;
-      const int j = (int)(k - t * tk);
-      unsigned char* base = rr.rec[q] + rl.roff[n] + t * rl.rbytes[n] + (int64_t)tk * 4;
-      if (q == 0) ((double*)base)[j] = r;
-      else if (q == 1) ((float2*)base)[j] = df_from_double(r);
-      else ((float*)base)[j] = (float)r;
-    }
-  }
 }
 
 __global__ void k_nu_prec(int N, const double* nu, float2* nudf, float* nu32) {
@@ -231,16 +212,9 @@ int hq_build_rates(hq_solver* h) {
   la.N = h->N;
   for (int i = 0; i < HQ_MAXN + 2; i++) la.off[i] = h->off[i];
   for (int i = 0; i <= HQ_MAXN; i++) la.lsize[i] = i <= h->N ? h->lsize[i] : 0;
-  RateRecords rr;
-  rr.rl[0] = h->b64.rl;
-  rr.rl[1] = h->bdf.rl;
-  rr.rl[2] = h->b32.rl;
-  rr.rec[0] = (unsigned char*)h->b64.rec;
-  rr.rec[1] = (unsigned char*)h->bdf.rec;
-  rr.rec[2] = (unsigned char*)h->b32.rec;
   k_rates<<<(unsigned)((h->Sp + 255) / 256), 256, 0, h->stream>>>(
       la, h->Sp, h->masks, h->nu, h->lam, lam_full, (double*)h->b64.r, (float2*)h->bdf.r,
-      (float*)h->b32.r, rr);
+      (float*)h->b32.r);
   HQ_LAUNCHED();
   HQ_CUDA(cudaMemcpyAsync(h->b64.nu, h->nu, sizeof(double) * h->N, cudaMemcpyDeviceToDevice,
                           h->stream));

@@ -25,17 +25,21 @@
 // the layer's scalar recursion and publishes c1, c2, lambda(n), mu(n) and the step
 // before it releases the others: the result is deterministic.
 //
-// Streaming.  Warp 0 copies the table rows, r_m and state masks of a tile of
-// consecutive states to shared memory with bulk asynchronous copies (cp.async.bulk,
-// completion on an mbarrier), up to kStages tiles ahead, across grid barriers too
-// (the table never changes); warps 1..7 consume the tiles and free each stage through
-// a second mbarrier.  Neighbour values are gathered through L2.  Each thread loads the
-// rank bases of its state's high-part neighbours once, in parallel, into its own
-// shared-memory slot, so no gather waits on a dependent table load.
+// Work.  Layer n is cut into items of at most 32 consecutive states of one rank block
+// (see HQ_ITEM_HI_BITS); items go round-robin to the warps of the grid.  A warp first
+// copies the two small blocks that hold its states' neighbours across a low-part unit,
+// (hi, w-1) of the (A, B) pairs of layer n-1 and (hi, w+1) of p of layer n+1, into its
+// own slot of shared memory with coalesced loads, so that the scattered part of the
+// gather reads shared memory; the positions there come precomputed per state (lidx).
+// Neighbours across a high-part unit, and the table rows, are read with coalesced loads
+// straight from global memory: one lane per state, consecutive states at consecutive
+// addresses.  Loads are issued in chunks before their values are used, so many are
+// in flight per thread.  There is no producer, no stage ring and no wait other than the
+// grid barrier.
 //
-// Every wait is bounded: a grid barrier or mbarrier that does not complete within its
-// iteration limit sets an error bit in DevScalars::flags and the kernel runs to its
-// end with in-bounds indices; the host reports HQ_ETIMEOUT.
+// The grid barrier's wait is bounded: a barrier that does not complete within its
+// iteration limit sets an error bit in DevScalars::flags and the kernel runs to its end
+// with in-bounds indices; the host reports HQ_ETIMEOUT.
 #include <stdlib.h>
 #include <string.h>
 
@@ -43,120 +47,54 @@
 
 namespace {
 
-constexpr int kThreads = HQ_THREADS;        // 256: warp 0 issues the bulk copies,
-constexpr int kConsumers = kThreads - 32;  // warps 1..7 consume the staged tiles
-constexpr int kStages = 2;
-static_assert(HQ_MAX_TILE == 2 * kConsumers, "tile records hold two states per consumer thread");
-constexpr int kMaxHi = HQ_MAXN - HQ_LO_BITS;  // high-part bits of a state mask
-constexpr int kPW = 6;                        // partial words per CTA per phase
+constexpr int kThreads = 512;             // 16 warps, two CTAs per SM at 64 registers
+constexpr int kWarps = kThreads / 32;
+constexpr int kPW = 6;                    // partial words per CTA per phase
 constexpr unsigned kSpinLimit = 1u << 24;
 
-// stage size per precision: four CTAs per SM with the rank-base slots
-template <class V> struct StageBytes { static constexpr int v = HQ_STAGE_WIDE; };
-template <> struct StageBytes<PolF32> { static constexpr int v = HQ_STAGE_F32; };
-// gathers in flight per thread (chunk length), within the 64-register budget
-template <class V> struct Chunk { static constexpr int v = 4; };
-template <> struct Chunk<PolF32> { static constexpr int v = 8; };
+// loads in flight per thread per chunk (busy, idle neighbours), within 64 registers
+template <class V> struct Chunk { static constexpr int b = 2, i = 2; };
+template <> struct Chunk<PolF32> { static constexpr int b = 4, i = 4; };
 
 // ---- PTX helpers ------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-               "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// L2 policies: the table streams through once per sweep (evict first); the
-// neighbour layers are gathered many times (evict last)
-__device__ __forceinline__ uint64_t policy_evict_first() {
-  uint64_t p;
-  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
-  return p;
-}
-__device__ __forceinline__ uint64_t policy_evict_last() {
-  uint64_t p;
-  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
-  return p;
-}
-// 1-D bulk copy global -> shared, completion counted on `bar`
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar,
-                                         uint64_t pol) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, "
-      "[%3], %4;" ::"r"(smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(pol)
-      : "memory");
-}
 __device__ __forceinline__ unsigned long long globaltimer_ns() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
-__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
-  unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
+// barrier arrival (acquire + release at gpu scope), release of the barrier, acquire fence
+__device__ __forceinline__ unsigned atom_add_acq_rel(unsigned* p, unsigned v) {
+  unsigned r;
+  asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], %2;" : "=r"(r) : "l"(p), "r"(v) : "memory");
+  return r;
 }
-// polling load: coherent at gpu scope without the acquire's L1 invalidation, so
-// spinning CTAs do not evict the cached rank tables of CTAs still working on the SM
+__device__ __forceinline__ void red_add_release(unsigned* p, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+// 16-byte asynchronous global -> shared copy through L2 only (it sees other CTAs' writes
+// made before the grid barrier), and the wait for all of this thread's such copies
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+               "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+// polling load: coherent at gpu scope without the acquire's L1 invalidation, so spinning
+// CTAs do not evict the cached data of CTAs still working on the SM
 __device__ __forceinline__ unsigned ld_relaxed_u32(const unsigned* p) {
   unsigned v;
   asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
 }
 
-// ---- loads of values that other CTAs wrote in this launch: from L2 (.cg), kept there -----
-__device__ __forceinline__ float ld_l2(const float* p, uint64_t pol) {
-  float v;
-  asm volatile("ld.global.cg.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
-  return v;
-}
-__device__ __forceinline__ float2 ld_l2(const float2* p, uint64_t pol) {
-  float2 v;
-  asm volatile("ld.global.cg.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;"
-               : "=f"(v.x), "=f"(v.y)
-               : "l"(p), "l"(pol));
-  return v;
-}
-__device__ __forceinline__ float4 ld_l2(const float4* p, uint64_t pol) {
-  float4 v;
-  asm volatile("ld.global.cg.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
-               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
-               : "l"(p), "l"(pol));
-  return v;
-}
-__device__ __forceinline__ double ld_l2(const double* p, uint64_t pol) {
-  double v;
-  asm volatile("ld.global.cg.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(p), "l"(pol));
-  return v;
-}
-__device__ __forceinline__ double2 ld_l2(const double2* p, uint64_t pol) {
-  double2 v;
-  asm volatile("ld.global.cg.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;"
-               : "=d"(v.x), "=d"(v.y)
-               : "l"(p), "l"(pol));
-  return v;
-}
+// ---- loads of values other CTAs wrote in this launch: from L2 (.cg); the table streams
+// through once per sweep (ld_stream, hq_internal.cuh)
 __device__ __forceinline__ double ld_l2(const double* p) { return __ldcg(p); }
 __device__ __forceinline__ float2 ld_l2(const float2* p) { return __ldcg(p); }
 __device__ __forceinline__ float ld_l2(const float* p) { return __ldcg(p); }
+__device__ __forceinline__ double2 ld_l2(const double2* p) { return __ldcg(p); }
+__device__ __forceinline__ float4 ld_l2(const float4* p) { return __ldcg(p); }
 
 // (A, B) pair storage per precision
 template <class V> struct Pair;
@@ -165,24 +103,18 @@ template <> struct Pair<PolF64> {
   __device__ static P pack(double a, double b) { return make_double2(a, b); }
   __device__ static double A(P p) { return p.x; }
   __device__ static double B(P p) { return p.y; }
-  __device__ static P ld(const P* q) { return __ldcg(q); }
-  __device__ static P ld(const P* q, uint64_t pol) { return __ldca(q); }
 };
 template <> struct Pair<PolDF> {
   typedef float4 P;
   __device__ static P pack(float2 a, float2 b) { return make_float4(a.x, a.y, b.x, b.y); }
   __device__ static float2 A(P p) { return make_float2(p.x, p.y); }
   __device__ static float2 B(P p) { return make_float2(p.z, p.w); }
-  __device__ static P ld(const P* q) { return __ldcg(q); }
-  __device__ static P ld(const P* q, uint64_t pol) { return __ldca(q); }
 };
 template <> struct Pair<PolF32> {
   typedef float2 P;
   __device__ static P pack(float a, float b) { return make_float2(a, b); }
   __device__ static float A(P p) { return p.x; }
   __device__ static float B(P p) { return p.y; }
-  __device__ static P ld(const P* q) { return __ldcg(q); }
-  __device__ static P ld(const P* q, uint64_t pol) { return __ldca(q); }
 };
 
 template <class V>
@@ -191,20 +123,28 @@ __device__ __forceinline__ typename V::T warp_sum(typename V::T v) {
   return v;
 }
 
+// position of the k-th low-part neighbour of a state in its staged block (lidx bytes)
+__device__ __forceinline__ int lo_pos(uint32_t w0, uint32_t w1, uint32_t w2, int k) {
+  const uint32_t wd = k < 4 ? w0 : (k < 8 ? w1 : w2);
+  return (int)((wd >> (8 * (k & 3))) & 0xffu);
+}
+
 struct PersistArgs {
   int N, L, H, nsweeps;
   double lam;
-  int64_t off[HQ_MAXN + 2];   // padded per-state offsets of the layers
-  int64_t toff[HQ_MAXN + 2];  // padded table offsets of the layers
+  int64_t Sp;
+  int64_t off[HQ_MAXN + 2];     // padded per-state offsets of the layers
+  int64_t toff[HQ_MAXN + 2];    // padded table offsets of the layers
   int64_t lsize[HQ_MAXN + 1];
-  int64_t lpad[HQ_MAXN + 1];  // table row stride of layer n
-  int tk[HQ_MAXN + 1];        // states per tile in layer n
-  int ntiles[HQ_MAXN + 1];
-  int64_t rbytes[HQ_MAXN + 1];  // bytes of a tile record of layer n
-  int64_t roff[HQ_MAXN + 2];    // first record of layer n
-  const unsigned char* rec;     // tile records: masks, r_m, table rows
+  int64_t lpad[HQ_MAXN + 1];    // table row stride of layer n
+  int ifirst[HQ_MAXN + 2];      // items of layer n: [ifirst[n], ifirst[n+1])
+  const uint4* items;
+  const uint32_t* masks;
+  const uint32_t* lidx;
   const uint32_t* RL;
   const uint32_t* RH;
+  const void* T;
+  const void* r;
   void* p;
   const void* nu;
   void* ab0;
@@ -213,59 +153,45 @@ struct PersistArgs {
   DevScalars* sc;
 };
 
-// work-item cursor of the bulk-copy producer: sweep k, layer n, tile t
-struct Cursor {
-  int k, n, t;
-};
-
-__device__ __forceinline__ bool cursor_fix(const PersistArgs& a, Cursor& c) {
-  while (c.t >= a.ntiles[c.n]) {
-    c.n++;
-    c.t = blockIdx.x;
-    if (c.n > a.N - 1) {
-      c.n = 1;
-      c.k++;
-    }
-    if (c.k >= a.nsweeps) return false;
-  }
-  return true;
-}
-
-// one bulk copy per tile: the tile's record is the exact image of the stage
 template <class V>
-__device__ void issue_tile(const PersistArgs& a, const Cursor& c, unsigned char* stage, uint64_t* bar) {
-  const int n = c.n;
-  const unsigned bytes = (unsigned)a.rbytes[n];
-  mbar_expect_tx(bar, bytes);
-  bulk_g2s(stage, a.rec + a.roff[n] + (int64_t)c.t * a.rbytes[n], bytes, bar, policy_evict_first());
-}
-
-template <class V>
-__global__ void __launch_bounds__(kThreads, 4) k_persist(PersistArgs a) {
+__global__ void __launch_bounds__(kThreads, 2) k_persist(PersistArgs a) {
   typedef typename V::T T;
   typedef Pair<V> PR;
   typedef typename PR::P P2;
-  constexpr int kStageBytes = StageBytes<V>::v;
-  constexpr int CH = Chunk<V>::v;
+  constexpr int CB = Chunk<V>::b, CI = Chunk<V>::i;
+  // per-warp slots: staged (A, B) block of layer n-1, then staged p block of layer n+1
   extern __shared__ __align__(128) unsigned char smem[];
-  unsigned char* stages = smem;
-  uint32_t* s_hb = (uint32_t*)(smem + kStages * kStageBytes);  // [H][kConsumers]
-  __shared__ __align__(8) uint64_t full_bar[kStages];   // tile landed (transaction count)
-  __shared__ __align__(8) uint64_t empty_bar[kStages];  // every consumer warp is done with it
+  __shared__ uint32_t s_RL[1 << HQ_LO_BITS];
+  __shared__ int s_binL[HQ_LO_BITS + 2];
   __shared__ double s_lam[HQ_MAXN + 1], s_mu[HQ_MAXN + 1];
   __shared__ T s_nu[HQ_MAXN];
-  __shared__ double s_red[kPW][kThreads / 32];
-  __shared__ double s_fold[kPW];
+  __shared__ double s_red[kPW][kWarps];
   __shared__ T s_lamT, s_one;
   __shared__ T s_c1, s_c2;
   __shared__ double s_step[2];
   __shared__ int s_last;
-  __shared__ unsigned s_gen;
+  __shared__ unsigned s_gen0;
 
   DevScalars* sc = a.sc;
   const int N = a.N, L = a.L, H = a.H;
   const unsigned G = gridDim.x;
-  const uint32_t* RL = a.RL;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const uint32_t lmask = (1u << L) - 1u, hmask = (1u << H) - 1u;
+  constexpr int kSlotD = HQ_MAX_BLOCK * (int)sizeof(P2) + 16, kSlotU = HQ_MAX_BLOCK * (int)sizeof(T) + 16;
+  unsigned char* slot_d = smem + (size_t)wid * (kSlotD + kSlotU);
+  unsigned char* slot_u = slot_d + kSlotD;
+  for (int i = threadIdx.x; i < (1 << L); i += blockDim.x) s_RL[i] = a.RL[i];
+  if (threadIdx.x <= L + 1) {
+    // C(L, i - 1): the sizes of the blocks (hi, w -/+ 1) are s_binL[w] and s_binL[w + 2]
+    const int i = threadIdx.x;
+    int c = 0;
+    if (i >= 1) {
+      double v = 1.0;
+      for (int q = 1; q <= i - 1; q++) v = v * (double)(L - (i - 1) + q) / (double)q;
+      c = (int)(v + 0.5);
+    }
+    s_binL[i] = c;
+  }
   if (threadIdx.x < N) s_nu[threadIdx.x] = ((const T*)a.nu)[threadIdx.x];
   if (threadIdx.x <= N) {
     s_lam[threadIdx.x] = sc->lam_n[threadIdx.x];
@@ -278,164 +204,123 @@ __global__ void __launch_bounds__(kThreads, 4) k_persist(PersistArgs a) {
     s_c2 = V::zero();
     s_step[0] = s_step[1] = 0.0;
     if (blockIdx.x == 0) sc->t_start = globaltimer_ns();
-    for (int i = 0; i < kStages; i++) {
-      mbar_init(&full_bar[i], 1);
-      mbar_init(&empty_bar[i], kConsumers / 32);
-    }
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    // no barrier of this launch completes before every CTA has arrived once
+    s_gen0 = ld_relaxed_u32(&sc->bar_gen);
   }
   __syncthreads();
 
-  // Tiles of this CTA are numbered in the order they are consumed (sweep, layer,
-  // tile); tile i uses stage i % kStages.  Thread 0 (warp 0) is the producer;
-  // warps 1..7 consume.  `phase_end` = number of tiles consumed by the end of the
-  // current phase, the same in every thread.
-  Cursor pc{0, 1, (int)blockIdx.x};
-  bool p_more = cursor_fix(a, pc);
-  long issued = 0, consumed = 0, phase_end = 0;
-  const bool producer = threadIdx.x == 0;
-  const bool consumer = threadIdx.x >= 32;
-  const int ctid = (int)threadIdx.x - 32;
-  // Issue tiles while a stage is free.  A stage is waited for only if the tile that
-  // occupies it is consumed in this phase: the consumers cannot free stages of a
-  // later phase before the grid barrier, so waiting for one would never end.
-  auto produce = [&]() {
-    while (p_more) {
-      if (issued >= kStages) {
-        const long occ = issued - kStages;
-        if (occ >= phase_end) break;
-        unsigned it = 0;
-        while (!mbar_try_wait(&empty_bar[issued % kStages], (unsigned)((occ / kStages) & 1))) {
-          if (++it > kSpinLimit) {
-            atomicOr(&sc->flags, 4);
-            break;
-          }
-        }
-      }
-      issue_tile<V>(a, pc, stages + (issued % kStages) * kStageBytes, &full_bar[issued % kStages]);
-      issued++;
-      pc.t += G;
-      p_more = cursor_fix(a, pc);
-    }
-  };
-
   const T* pv = (const T*)a.p;
-  const uint64_t keep = policy_evict_last();  // L2 policy of the gathered neighbour values
   T* pw = (T*)a.p;
-  const int64_t nthreads = (int64_t)G * blockDim.x;
-  const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const T* Tt = (const T*)a.T;
+  const T* rt = (const T*)a.r;
+  const int gwarp = (int)blockIdx.x * kWarps + wid;
+  const int nwarps = (int)G * kWarps;
   int gphase = 0;  // phase counter within this launch
 
   // finalise layer lf from the (A, B) buffer `abf`: p = c1 A + c2 B, |p - p_old|
-  auto finalize = [&](int lf, const P2* abf, double& md) {
+  auto finalize = [&](int lf, const P2* abf, float& md) {
     const T c1 = s_c1, c2 = s_c2;
     T* pl = pw + a.off[lf];
     const int64_t Lf = a.lsize[lf];
+    const int64_t nthreads = (int64_t)G * blockDim.x;
 #pragma unroll 4
-    for (int64_t k = gtid; k < Lf; k += nthreads) {
-      const P2 q = PR::ld(abf + k);
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < Lf; k += nthreads) {
+      const P2 q = ld_l2(abf + k);
       const T old = ld_l2(pl + k);
       const T v = V::add(V::mul(c1, PR::A(q)), V::mul(c2, PR::B(q)));
-      md = fmax(md, V::absdiff(v, old));
+      md = fmaxf(md, V::absdiff(v, old));
       pl[k] = v;
     }
   };
 
-  // Write this CTA's partials, then the grid barrier.  The last CTA to arrive folds
-  // all partials in CTA order, solves the scalar recursion of layer lg (if lg > 0)
-  // and publishes the result before it releases the others.  ks: sweep of the layer
-  // finalised in this phase (its step goes into s_step).
-  auto sync_phase = [&](T sA, T sB, T sa, T sb, double md, int lg, int ks) {
+  // Write this CTA's partials, then the grid barrier.  Arrivals count up on bar_count
+  // (zeroed before the launch): the CTA whose arrival completes phase g's count folds
+  // all partials in CTA order, solves the scalar recursion of layer lg (if lg > 0),
+  // publishes the result and then bumps bar_gen with release semantics; the others wait
+  // for bar_gen to reach gen0 + g + 1.  ks: sweep of the layer finalised in this phase
+  // (its step goes into s_step).
+  auto sync_phase = [&](T sA, T sB, T sa, T sb, float md, int lg, int ks) {
     const int buf = gphase & 1;
+    double* part = a.partials + (size_t)buf * kPW * G;  // [word][CTA]
     {
       T w4[4] = {sA, sB, sa, sb};
-      const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
       for (int i = 0; i < 4; i++) {
         const T v = warp_sum<V>(w4[i]);
         if (lane == 0) s_red[i][wid] = V::to_d(v);
       }
-      for (int m = 16; m > 0; m >>= 1) md = fmax(md, __shfl_xor_sync(0xffffffffu, md, m));
-      if (lane == 0) s_red[4][wid] = md;
-      __syncthreads();
-      if (threadIdx.x < 5) {
-        double t = 0.0;
-        for (int q = 0; q < (int)(blockDim.x >> 5); q++)
-          t = (threadIdx.x == 4) ? fmax(t, s_red[threadIdx.x][q]) : t + s_red[threadIdx.x][q];
-        a.partials[((size_t)buf * G + blockIdx.x) * kPW + threadIdx.x] = t;
-      }
+      for (int m = 16; m > 0; m >>= 1) md = fmaxf(md, __shfl_xor_sync(0xffffffffu, md, m));
+      if (lane == 0) s_red[4][wid] = (double)md;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-      s_gen = ld_relaxed_u32(&sc->bar_gen);
-      __threadfence();
-      s_last = atomicAdd(&sc->bar_count, 1u) == G - 1;
-    }
-    __syncthreads();
-    if (s_last) {
-      // fold every CTA's partials in CTA order
-      const double* part = a.partials + (size_t)buf * G * kPW;
-      double v[kPW];
+    if (wid == 0) {
+      // warp 0 folds the kWarps warp results of each word (few FP64 operations)
+      double v[5];
 #pragma unroll
-      for (int w = 0; w < kPW; w++) v[w] = 0.0;
-      for (unsigned b = threadIdx.x; b < G; b += blockDim.x) {
-#pragma unroll
-        for (int w = 0; w < 5; w++) {
-          const double x = __ldcg(part + (size_t)b * kPW + w);
-          v[w] = (w == 4) ? fmax(v[w], x) : v[w] + x;
-        }
-      }
+      for (int w = 0; w < 5; w++) v[w] = lane < kWarps ? s_red[w][lane] : 0.0;
 #pragma unroll
       for (int w = 0; w < 5; w++)
-        for (int m = 16; m > 0; m >>= 1) {
+        for (int m = kWarps / 2; m > 0; m >>= 1) {
           const double o = __shfl_xor_sync(0xffffffffu, v[w], m);
           v[w] = (w == 4) ? fmax(v[w], o) : v[w] + o;
         }
-      const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
       if (lane == 0) {
+        // this thread writes the CTA's partials, so its release covers them
 #pragma unroll
-        for (int w = 0; w < 5; w++) s_red[w][wid] = v[w];
+        for (int w = 0; w < 5; w++) part[(size_t)w * G + blockIdx.x] = v[w];
+        const unsigned old = atom_add_acq_rel(&sc->bar_count, 1u);
+        s_last = old == G * (unsigned)(gphase + 1) - 1u;
       }
-      __syncthreads();
-      if (threadIdx.x < 5) {
-        double t = 0.0;
-        for (int q = 0; q < (int)(blockDim.x >> 5); q++)
-          t = (threadIdx.x == 4) ? fmax(t, s_red[threadIdx.x][q]) : t + s_red[threadIdx.x][q];
-        s_fold[threadIdx.x] = t;
+    }
+    __syncthreads();
+    if (s_last) {
+      // fold every CTA's partials in CTA order: warp w < 5 takes word w
+      if (wid < 5) {
+        double v = 0.0;
+        for (unsigned b = lane; b < G; b += 32) {
+          const double x = __ldcg(part + (size_t)wid * G + b);
+          v = (wid == 4) ? fmax(v, x) : v + x;
+        }
+        for (int m = 16; m > 0; m >>= 1) {
+          const double o = __shfl_xor_sync(0xffffffffu, v, m);
+          v = (wid == 4) ? fmax(v, o) : v + o;
+        }
+        if (lane == 0) s_red[wid][0] = v;
       }
       __syncthreads();
       if (threadIdx.x == 0) {
+        double f[5];
+#pragma unroll
+        for (int w = 0; w < 5; w++) f[w] = s_red[w][0];
         double* pub = sc->pub[buf];
         if (lg > 0) {
           // closed-form limit of the inner loop (Eq. 12 and 14), then Eq. (13)
           const double alpha = 1.0 / s_lam[lg - 1];
           const double beta = s_lam[lg] / s_mu[lg + 1];
-          const double aa = alpha * s_fold[0], bb = beta * s_fold[1];
+          const double aa = alpha * f[0], bb = beta * f[1];
           const double mustar = bb / (1.0 - aa);
           const double c1 = alpha * mustar;
           pub[0] = c1;
           pub[1] = beta;
-          pub[2] = a.lam * (c1 * s_fold[2] + beta * s_fold[3]);
+          pub[2] = a.lam * (c1 * f[2] + beta * f[3]);
           pub[3] = mustar;
           if (!isfinite(mustar) || !(aa < 1.0)) atomicOr(&sc->flags, 1);
         }
-        pub[4] = s_fold[4];
+        pub[4] = f[4];
         if (gphase < 64) sc->t_phase[gphase] = globaltimer_ns();
-        __threadfence();
-        atomicExch(&sc->bar_count, 0u);
-        __threadfence();
-        atomicAdd(&sc->bar_gen, 1u);
+        red_add_release(&sc->bar_gen, 1u);
       }
     } else if (threadIdx.x == 0) {
+      const unsigned target = s_gen0 + (unsigned)gphase + 1u;
       unsigned it = 0;
-      while (ld_relaxed_u32(&sc->bar_gen) == s_gen) {
+      while ((int)(ld_relaxed_u32(&sc->bar_gen) - target) < 0) {
         if (*(volatile int*)&sc->flags & 6) break;  // an earlier wait gave up: do not wait again
         if (++it > kSpinLimit) {
           atomicOr(&sc->flags, 2);
           break;
         }
       }
-      __threadfence();
+      fence_acq_rel_gpu();
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -455,128 +340,147 @@ __global__ void __launch_bounds__(kThreads, 4) k_persist(PersistArgs a) {
   for (int k = 0; k < a.nsweeps; k++) {
     for (int n = 1; n <= N - 1; n++) {
       if (threadIdx.x == 0 && n == 1) s_step[k & 1] = 0.0;  // sweep k starts
-      // the layer this phase finalises: gathered in the previous phase
+      // the layer this phase finalises: gathered in the previous phase (not read in this one)
       const int fin_layer = gphase == 0 ? -1 : (n == 1 ? N - 1 : n - 1);
-      // -- gather layer n -------------------------------------------------------------------
       const P2* ab_prev = (const P2*)(((gphase + 1) & 1) ? a.ab1 : a.ab0);
       P2* ab_cur = (P2*)((gphase & 1) ? a.ab1 : a.ab0);
       const T* p_up = pv + a.off[n + 1];
-      const int tk = a.tk[n];
-      const int64_t Ln = a.lsize[n];
-      const T c1 = s_c1, c2 = s_c2;
-      const int nb = n == 1 ? 0 : n;  // busy neighbours read from the (A, B) pairs
-      const int ni = N - n;           // idle neighbours
+      float md = 0.f;
+      if (fin_layer > 0) finalize(fin_layer, ab_prev, md);
+      // -- gather layer n -------------------------------------------------------------------
       T sA = V::zero(), sB = V::zero(), sa = V::zero(), sb = V::zero();
-      const long my_tiles =
-          a.ntiles[n] > (int)blockIdx.x ? (long)((a.ntiles[n] - 1 - (int)blockIdx.x) / (int)G) + 1 : 0;
-      phase_end = consumed + my_tiles;
-      if (producer) produce();
-      for (int t = blockIdx.x; consumer && t < a.ntiles[n]; t += G) {
-        const long item = consumed++;
-        const int st = (int)(item % kStages);
-        unsigned char* stage = stages + st * kStageBytes;
+      const int64_t lp = a.lpad[n];
+      const int it_end = a.ifirst[n + 1];
+      int it = a.ifirst[n] + gwarp;
+      uint4 dnext = it < it_end ? __ldg(a.items + it) : make_uint4(0u, 0u, 0u, 0u);
+      for (; it < it_end; it += nwarps) {
+        const uint4 d = dnext;
+        if (it + nwarps < it_end) dnext = __ldg(a.items + it + nwarps);  // next item, ahead
+        const uint32_t rank0 = d.x;
+        const uint32_t hi = d.y & ((1u << HQ_ITEM_HI_BITS) - 1u);
+        const int w = (int)((d.y >> HQ_ITEM_HI_BITS) & 0xfu);
+        const int count = (int)((d.y >> 24) & 0x1fu) + 1;
+        // rank bases of the high-part neighbour blocks: lane j holds RH[hi ^ 2^j][w]
+        const uint32_t hbl = lane < H ? __ldg(a.RH + (size_t)(hi ^ (1u << lane)) * (L + 1) + w) : 0u;
+        // this lane's state (lanes past the item repeat its first state and discard it)
+        const bool act = lane < count;
+        const uint32_t kq = rank0 + (act ? (uint32_t)lane : 0u);
+        const int64_t gi = a.off[n] + kq;
+        const uint32_t x = __ldg(a.masks + gi);
+        const uint32_t iw0 = __ldg(a.lidx + gi), iw1 = __ldg(a.lidx + a.Sp + gi),
+                       iw2 = __ldg(a.lidx + 2 * a.Sp + gi);
+        const T rv = __ldg(rt + gi);
+        const T* tcol = Tt + a.toff[n] + kq;  // table slot s at tcol[s * lp]
+        // stage the low-part neighbour blocks in this warp's slot with 16-byte asynchronous
+        // copies: a block's copy starts at the 16-byte boundary at or below its first
+        // element (offset `dd` / `du` elements into the slot) and covers whole 16-byte units
+        const P2* sdn;
+        const T* sup;
         {
-          unsigned it = 0;
-          while (!mbar_try_wait(&full_bar[st], (unsigned)((item / kStages) & 1))) {
-            if (++it > kSpinLimit) {
-              atomicOr(&sc->flags, 4);
-              break;
+          const int dc = (n > 1 && w > 0) ? s_binL[w] : 0;
+          const int uc = w < L ? s_binL[w + 2] : 0;
+          const unsigned char* gd = (const unsigned char*)(ab_prev + d.z);
+          const unsigned char* gu = (const unsigned char*)(p_up + d.w);
+          const int od = (int)((uintptr_t)gd & 15u), ou = (int)((uintptr_t)gu & 15u);
+          const int cd = dc ? (od + dc * (int)sizeof(P2) + 15) >> 4 : 0;
+          const int cu = uc ? (ou + uc * (int)sizeof(T) + 15) >> 4 : 0;
+          for (int c = lane; c < cd; c += 32) cp_async16(slot_d + 16 * c, gd - od + 16 * c);
+          for (int c = lane; c < cu; c += 32) cp_async16(slot_u + 16 * c, gu - ou + 16 * c);
+          cp_async_wait_all();
+          sdn = (const P2*)(slot_d + od);
+          sup = (const T*)(slot_u + ou);
+        }
+        const uint32_t lo = x & lmask;
+        const uint32_t rl = s_RL[lo];
+        __syncwarp();
+        T UA = V::zero(), UB = V::zero(), D = V::zero();
+        // Busy neighbours in table-slot order (increasing unit): w low-part ones from the
+        // staged block, then the high part at rank RH[hi ^ 2^c][w] + RL[lo] of layer n-1.
+        // Idle neighbours, rate nu_u, in increasing unit order: L - w low-part ones from the
+        // staged block, then the high part at rank RH[hi ^ 2^c][w] + RL[lo] of layer n+1.
+        // One chunk takes CB busy and CI idle neighbours, so both chains advance together.
+        {
+          const int nb = n > 1 ? n : 0, ni = N - n, nl = L - w;
+          uint32_t yb = hi, yl = ~lo & lmask, yh = ~hi & hmask;
+          for (int sb0 = 0, si0 = 0; sb0 < nb || si0 < ni; sb0 += CB, si0 += CI) {
+            P2 q[CB];
+            T tv[CB], v[CI];
+            const uint32_t yl0 = yl, yh0 = yh;
+#pragma unroll
+            for (int j = 0; j < CB; j++) {
+              const int s = sb0 + j;
+              if (s < nb) {
+                tv[j] = ld_stream(tcol + s * lp);
+                if (s < w) {
+                  q[j] = sdn[lo_pos(iw0, iw1, iw2, s)];
+                } else {
+                  const int c = __ffs(yb) - 1;
+                  yb &= yb - 1;
+                  q[j] = ld_l2(ab_prev + __shfl_sync(0xffffffffu, hbl, c) + rl);
+                }
+              }
+            }
+#pragma unroll
+            for (int j = 0; j < CI; j++) {
+              const int s = si0 + j;
+              if (s < ni) {
+                if (s < nl) {
+                  yl &= yl - 1;
+                  v[j] = sup[lo_pos(iw0, iw1, iw2, w + s)];
+                } else {
+                  const int c = __ffs(yh) - 1;
+                  yh &= yh - 1;
+                  v[j] = ld_l2(p_up + __shfl_sync(0xffffffffu, hbl, c) + rl);
+                }
+              }
+            }
+#pragma unroll
+            for (int j = 0; j < CB; j++) {
+              if (sb0 + j < nb) {
+                V::fma_acc(UA, PR::A(q[j]), tv[j]);
+                V::fma_acc(UB, PR::B(q[j]), tv[j]);
+              }
+            }
+            uint32_t zl = yl0, zh = yh0;  // replay the unit order for the rates nu_u
+#pragma unroll
+            for (int j = 0; j < CI; j++) {
+              const int s = si0 + j;
+              if (s < ni) {
+                int u;
+                if (s < nl) {
+                  u = __ffs(zl) - 1;
+                  zl &= zl - 1;
+                } else {
+                  u = L + __ffs(zh) - 1;
+                  zh &= zh - 1;
+                }
+                V::fma_acc(D, v[j], s_nu[u]);
+              }
             }
           }
         }
-        const int64_t k0 = (int64_t)t * tk;
-        const int cnt = (int)min((int64_t)tk, Ln - k0);
-        for (int i = ctid; i < cnt; i += kConsumers) {
-          const uint32_t x = ((const uint32_t*)stage)[i];
-          const T rv = ((const T*)(stage + tk * 4))[i];
-          const T* trow = (const T*)(stage + tk * 4 + tk * (int)sizeof(T));
-          const uint32_t lo = x & ((1u << L) - 1u), hi = x >> L;
-          const int w = __popc(lo);
-          const uint32_t* rh = a.RH + (size_t)hi * (L + 1);
-          const uint32_t rl = __ldg(RL + lo);
-          const uint32_t base_dn = w > 0 ? __ldg(rh + w - 1) : 0u;
-          const uint32_t base_up = w < L ? __ldg(rh + w + 1) : 0u;
-          // rank bases of the neighbours that differ in a high-part unit j: all loads
-          // issued together, kept in this thread's shared-memory slot
-#pragma unroll
-          for (int j = 0; j < kMaxHi; j++)
-            if (j < H) s_hb[j * kConsumers + ctid] = __ldg(a.RH + (size_t)(hi ^ (1u << j)) * (L + 1) + w);
-          // Neighbours in chunks of CH: all ranks of a chunk, then all its gathers, then
-          // the accumulation, so CH gathers are in flight before the first is used.
-          // The chunk bounds depend only on n: no divergence.
-          T UA = V::zero(), UB = V::zero(), D = V::zero();
-          // busy neighbours: layer n-1, table slot s
-          uint32_t yb = x;
-          for (int s0 = 0; s0 < nb; s0 += CH) {
-            P2 q[CH];
-#pragma unroll
-            for (int j = 0; j < CH; j++) {
-              if (s0 + j < nb) {
-                const int b = __ffs(yb) - 1;
-                yb &= yb - 1;
-                const uint32_t rk = b < L ? __ldg(RL + (lo ^ (1u << b))) + base_dn
-                                          : rl + s_hb[(b - L) * kConsumers + ctid];
-                q[j] = PR::ld(ab_prev + rk, keep);
-              }
-            }
-#pragma unroll
-            for (int j = 0; j < CH; j++) {
-              if (s0 + j < nb) {
-                const T tv = trow[(s0 + j) * tk + i];
-                V::fma_acc(UA, PR::A(q[j]), tv);
-                V::fma_acc(UB, PR::B(q[j]), tv);
-              }
-            }
-          }
-          // idle neighbours: layer n+1, rate nu_u
-          uint32_t yi = ~x & ((1u << N) - 1u);
-          for (int s0 = 0; s0 < ni; s0 += CH) {
-            T pvv[CH];
-            uint32_t ysave = yi;
-#pragma unroll
-            for (int j = 0; j < CH; j++) {
-              if (s0 + j < ni) {
-                const int b = __ffs(yi) - 1;
-                yi &= yi - 1;
-                const uint32_t rk = b < L ? __ldg(RL + (lo | (1u << b))) + base_up
-                                          : rl + s_hb[(b - L) * kConsumers + ctid];
-                pvv[j] = __ldca(p_up + rk);
-              }
-            }
-#pragma unroll
-            for (int j = 0; j < CH; j++) {
-              if (s0 + j < ni) {
-                const int b = __ffs(ysave) - 1;
-                ysave &= ysave - 1;
-                V::fma_acc(D, pvv[j], s_nu[b]);
-              }
-            }
-          }
-          // up-inflow: layer 0 is the empty state with p_0 = 1
-          const T U = n == 1 ? trow[i] : V::add(V::mul(c1, V::norm(UA)), V::mul(c2, V::norm(UB)));
-          D = V::norm(D);
-          const T q = V::sub(s_one, V::mul(s_lamT, rv));  // mu_m r_m = 1 - lambda r_m
-          const T A = V::mul(U, rv), B = V::mul(D, rv);
-          ab_cur[k0 + i] = PR::pack(A, B);
-          sA = V::add(sA, V::mul(U, q));
-          sB = V::add(sB, V::mul(D, q));
+        // up-inflow: layer 0 is the empty state with p_0 = 1
+        const T U = n == 1 ? ld_stream(tcol)
+                           : V::add(V::mul(s_c1, V::norm(UA)), V::mul(s_c2, V::norm(UB)));
+        D = V::norm(D);
+        const T qm = V::sub(s_one, V::mul(s_lamT, rv));  // mu_m r_m = 1 - lambda r_m
+        const T A = V::mul(U, rv), B = V::mul(D, rv);
+        if (act) {
+          ab_cur[kq] = PR::pack(A, B);
+          sA = V::add(sA, V::mul(U, qm));
+          sB = V::add(sB, V::mul(D, qm));
           sa = V::add(sa, A);
           sb = V::add(sb, B);
         }
-        __syncwarp();
-        if ((threadIdx.x & 31) == 0) mbar_arrive(&empty_bar[st]);  // this warp is done
+        __syncwarp();  // the slot is restaged by the next item
       }
-      if (!consumer) consumed = phase_end;
-      // -- finalise the layer gathered in the previous phase ------------------------------
-      double md = 0.0;
-      if (fin_layer > 0) finalize(fin_layer, ab_prev, md);
       sync_phase(sA, sB, sa, sb, md, n, n >= 2 ? k : k - 1);
     }
   }
   // closing phase: final values of layer N-1 of the last sweep
   if (gphase > 0) {
     const int kl = a.nsweeps - 1;
-    double md = 0.0;
+    float md = 0.f;
     finalize(N - 1, (const P2*)(((gphase + 1) & 1) ? a.ab1 : a.ab0), md);
     sync_phase(V::zero(), V::zero(), V::zero(), V::zero(), md, -1, kl);
     if (threadIdx.x == 0 && blockIdx.x == 0) {
@@ -598,14 +502,12 @@ int g_nsm = 0;
 template <class V>
 int launch_persist(hq_solver* h, int nsweeps, cudaEvent_t ev0, cudaEvent_t ev1) {
   typedef typename V::T T;
-  constexpr int kStageBytes = StageBytes<V>::v;
+  typedef typename Pair<V>::P P2;
   const int slot = V::kind == HQ_PREC_FP64 ? 0 : (V::kind == HQ_PREC_DF64 ? 1 : 2);
-  const size_t smem_max = (size_t)kStages * kStageBytes + (size_t)kMaxHi * kConsumers * 4;
-  const size_t smem = (size_t)kStages * kStageBytes + (size_t)h->H * kConsumers * 4;
+  const size_t smem = (size_t)kWarps * (HQ_MAX_BLOCK * (sizeof(P2) + sizeof(T)) + 32);
   if (!g_nsm) HQ_CUDA(cudaDeviceGetAttribute(&g_nsm, cudaDevAttrMultiProcessorCount, h->dev));
   if (!g_occ[slot]) {
-    HQ_CUDA(cudaFuncSetAttribute(k_persist<V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem_max));
+    HQ_CUDA(cudaFuncSetAttribute(k_persist<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   }
   int occ = 0;
   HQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_persist<V>, kThreads, smem));
@@ -615,10 +517,15 @@ int launch_persist(hq_solver* h, int nsweeps, cudaEvent_t ev0, cudaEvent_t ev1) 
   }
   g_occ[slot] = occ;
   const int G = g_nsm * occ;
+  if ((int64_t)G * (nsweeps * (int64_t)(h->N - 1) + 1) >= ((int64_t)1 << 31)) {
+    hq_set_error("too many barrier arrivals for one launch");
+    return HQ_EINVAL;
+  }
   if ((int64_t)G * kPW * 2 > h->partials_len) {
     hq_set_error("partials buffer too small for the persistent grid");
     return HQ_ECUDA;
   }
+  PrecBufs& b = hq_bufs(h, V::kind);
   PersistArgs a;
   memset(&a, 0, sizeof(a));
   a.N = h->N;
@@ -626,30 +533,23 @@ int launch_persist(hq_solver* h, int nsweeps, cudaEvent_t ev0, cudaEvent_t ev1) 
   a.H = h->H;
   a.nsweeps = nsweeps;
   a.lam = h->lam;
+  a.Sp = h->Sp;
   for (int i = 0; i < HQ_MAXN + 2; i++) {
     a.off[i] = h->off[i];
     a.toff[i] = h->toff[i];
-  }
-  PrecBufs& b = hq_bufs(h, V::kind);
-  if (b.rl.esize != (int)sizeof(T)) {
-    hq_set_error("tile records do not match the sweep precision");
-    return HQ_ECUDA;
+    a.ifirst[i] = h->ifirst[i];
   }
   for (int n = 0; n <= HQ_MAXN; n++) {
     a.lsize[n] = n <= h->N ? h->lsize[n] : 0;
     a.lpad[n] = n <= h->N ? h->lpad[n] : 0;
-    a.tk[n] = b.rl.tk[n];
-    a.ntiles[n] = b.rl.ntiles[n];
-    a.rbytes[n] = b.rl.rbytes[n];
-    if (b.rl.rbytes[n] > kStageBytes) {
-      hq_set_error("a tile record is larger than a shared-memory stage");
-      return HQ_ECUDA;
-    }
   }
-  for (int n = 0; n < HQ_MAXN + 2; n++) a.roff[n] = b.rl.roff[n];
-  a.rec = (const unsigned char*)b.rec;
+  a.items = h->items;
+  a.masks = h->masks;
+  a.lidx = h->lidx;
   a.RL = h->RL;
   a.RH = h->RH;
+  a.T = b.T;
+  a.r = b.r;
   a.p = b.p;
   a.nu = b.nu;
   a.ab0 = h->ab;
@@ -677,7 +577,18 @@ PrecBufs& hq_bufs(hq_solver* h, int prec) {
 
 int hq_run_sweeps(hq_solver* h, int prec, int nsweeps, cudaEvent_t ev0, cudaEvent_t ev1) {
   if (h->N < 2 || nsweeps < 1) return HQ_OK;
-  if (prec == HQ_PREC_FP64) return launch_persist<PolF64>(h, nsweeps, ev0, ev1);
-  if (prec == HQ_PREC_DF64) return launch_persist<PolDF>(h, nsweeps, ev0, ev1);
-  return launch_persist<PolF32>(h, nsweeps, ev0, ev1);
+  // the barrier's arrival count (grid size x phases of a launch) stays below 2^31
+  const int64_t per = ((int64_t)1 << 31) / ((int64_t)152 * 8 * (h->N - 1) + 1) - 1;
+  const int cap = per > (1 << 20) ? (1 << 20) : (per < 1 ? 1 : (int)per);
+  for (int done = 0; done < nsweeps;) {
+    const int k = nsweeps - done < cap ? nsweeps - done : cap;
+    cudaEvent_t e0 = done == 0 ? ev0 : nullptr, e1 = done + k == nsweeps ? ev1 : nullptr;
+    int rc;
+    if (prec == HQ_PREC_FP64) rc = launch_persist<PolF64>(h, k, e0, e1);
+    else if (prec == HQ_PREC_DF64) rc = launch_persist<PolDF>(h, k, e0, e1);
+    else rc = launch_persist<PolF32>(h, k, e0, e1);
+    if (rc != HQ_OK) return rc;
+    done += k;
+  }
+  return HQ_OK;
 }

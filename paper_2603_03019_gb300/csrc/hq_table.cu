@@ -163,22 +163,11 @@ struct EmitArgs {
   int64_t toff[HQ_MAXN + 2];  // padded table layer starts
   int64_t lsize[HQ_MAXN + 1];
   int64_t lpad[HQ_MAXN + 1];  // row stride
-  RecLayout rl[3];            // tile records: FP64, DF64, FP32
 };
-
-// position of state k of layer n inside its tile record: (record base, slot j, tile size)
-__device__ __forceinline__ unsigned char* rec_slot(unsigned char* rec, const RecLayout& rl, int n,
-                                                   int64_t k, int* j, int* tk) {
-  *tk = rl.tk[n];
-  const int64_t t = k / *tk;
-  *j = (int)(k - t * *tk);
-  return rec + rl.roff[n] + t * rl.rbytes[n];
-}
 
 // one thread per state of layers 1..N: slot s <- F_{c_s}(m - c_s)
 __global__ void k_emit(EmitArgs a, int64_t S, const uint32_t* masks, const double* zeta,
-                       double* T64, unsigned char* rec64, unsigned char* recdf,
-                       unsigned char* rec32) {
+                       double* T64) {
   int64_t g = a.off[1] + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= S) return;
   int n = 1;
@@ -188,30 +177,10 @@ __global__ void k_emit(EmitArgs a, int64_t S, const uint32_t* masks, const doubl
   int64_t Ln = a.lpad[n];
   int64_t half = (int64_t)1 << (a.N - 1);
   uint32_t x = masks[g];
-  // tile records of the sweep (layers 1..N-1): mask, then table rows
-  const bool in_sweep = n <= a.N - 1;
-  unsigned char* r64 = nullptr;
-  unsigned char* rdf = nullptr;
-  unsigned char* r32 = nullptr;
-  int j64 = 0, jdf = 0, j32 = 0, t64 = 0, tdf = 0, t32 = 0;
-  if (in_sweep) {
-    r64 = rec_slot(rec64, a.rl[0], n, k, &j64, &t64);
-    rdf = rec_slot(recdf, a.rl[1], n, k, &jdf, &tdf);
-    r32 = rec_slot(rec32, a.rl[2], n, k, &j32, &t32);
-    ((uint32_t*)r64)[j64] = x;
-    ((uint32_t*)rdf)[jdf] = x;
-    ((uint32_t*)r32)[j32] = x;
-  }
   int s = 0;
   for (uint32_t y = x; y; y &= y - 1, s++) {
     int u = __ffs(y) - 1;
-    double v = __ldg(zeta + (int64_t)u * half + squeeze_bit(x, u));
-    T64[a.toff[n] + (int64_t)s * Ln + k] = v;
-    if (in_sweep) {
-      ((double*)(r64 + t64 * 4 + t64 * 8))[(int64_t)s * t64 + j64] = v;
-      ((float2*)(rdf + tdf * 4 + tdf * 8))[(int64_t)s * tdf + jdf] = df_from_double(v);
-      ((float*)(r32 + t32 * 4 + t32 * 4))[(int64_t)s * t32 + j32] = (float)v;
-    }
+    T64[a.toff[n] + (int64_t)s * Ln + k] = __ldg(zeta + (int64_t)u * half + squeeze_bit(x, u));
   }
 }
 
@@ -235,13 +204,9 @@ int hq_build_table(hq_solver* h) {
     a.lsize[i] = i <= N ? h->lsize[i] : 0;
     a.lpad[i] = i <= N ? h->lpad[i] : 0;
   }
-  a.rl[0] = h->b64.rl;
-  a.rl[1] = h->bdf.rl;
-  a.rl[2] = h->b32.rl;
   int64_t cnt = h->Sp - h->off[1];
   k_emit<<<(unsigned)((cnt + 255) / 256), 256, 0, h->stream>>>(
-      a, h->Sp, h->masks, h->zeta, (double*)h->b64.T, (unsigned char*)h->b64.rec,
-      (unsigned char*)h->bdf.rec, (unsigned char*)h->b32.rec);
+      a, h->Sp, h->masks, h->zeta, (double*)h->b64.T);
   HQ_LAUNCHED();
   return HQ_OK;
 }
