@@ -42,6 +42,14 @@ WORKLOADS = {
     "n20": lambda seed: I.mixed_n20(seed, 0.6),
     "n10": lambda seed: I.small_loss_n10(seed),
 }
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per algorithmic byte of the
+# FP32 sweep kernel, from one ncu capture of a smaller case of the same kernel; the
+# bench's launch is too large to capture, so its traffic is this ratio times its
+# algorithmic bytes (traffic grows in proportion to the states swept).  None once the
+# kernel has changed since the capture.
+SWEEP_DRAM_PER_ALG_BYTE = 297.768e6 / 251658120
+TRAFFIC_SOURCE = ("ncu --set full of one FP32 sweep at N=22 (profiles/k_persist_fp32_n22_set_full.md): "
+                  "297.8 MB DRAM for 251.7 MB algorithmic, scaled by algorithmic bytes")
 BASE_SEED = {"n24": 3001, "n23": 3001, "n22": 3001, "n20": 2001, "n10": 1001}
 
 
@@ -361,10 +369,13 @@ def run_ours(args):
                                   "achieved_gbs": round(ach, 1), "frac": round(ach / peak, 4)}
             # the headline path spends most of its sweeps in FP32
             d = per_prec["fp32"]
+            traffic = (SWEEP_DRAM_PER_ALG_BYTE * 8 * d["bytes_per_sweep"]
+                       if SWEEP_DRAM_PER_ALG_BYTE else None)
             roof = {"bound": "hbm", "kernel": "k_persist<PolF32>: one launch = 8 FP32 sweeps "
                     "(all layers 1..N-1, one grid barrier per layer)",
                     "achieved": d["achieved_gbs"], "peak": peak, "unit": "GB/s",
-                    "frac": d["frac"], "peak_kind": f"{kind} copy bandwidth", "traffic": None,
+                    "frac": d["frac"], "peak_kind": f"{kind} copy bandwidth", "traffic": traffic,
+                    "traffic_source": TRAFFIC_SOURCE,
                     "bytes_per_launch": 8 * d["bytes_per_sweep"],
                     "ms_per_launch": round(8 * d["ms_per_sweep"], 4), "per_precision": per_prec}
 
