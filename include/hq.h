@@ -207,6 +207,43 @@ double hq_sweep_bytes(const hq_solver* h, int precision);
 int hq_dispatch_table_static(int N, int J, const double* lambda_j, const int32_t* pref,
                              double* T, void* stream);
 
+/* ---- batched solves ----------------------------------------------------------------
+ * Algorithm 1 (Sec. 3.2, Eq. 12-14) on many independent instances of uneven N at once.
+ * The paper solves one instance at a time; the batch runs layer n of every instance in
+ * the same phase of one persistent launch (a device-side grid barrier between phases),
+ * so that small instances, whose per-layer work cannot fill the GPU, share it.
+ *
+ * hq_batch_create: solvers[0..count-1] are loaded solvers (hq_load succeeded, N >= 2)
+ *   on the current device; they are borrowed (not owned) and must outlive the batch.
+ *   stream: a cudaStream_t, or NULL for a stream of the batch's own.  Builds the
+ *   combined work lists (host memory for the build, device memory for the lists).
+ *   Errors: HQ_EINVAL (NULL, count < 1, N < 2, another device), HQ_ESTATE (a solver not
+ *   loaded), HQ_ENOMEM.
+ * hq_batch_tune: the autotuner.  Times each kernel variant (chunk widths of the gathers,
+ *   CTAs per SM) for `sweeps` sweeps of `precision` (HQ_PREC_FP64, _DF64 or _FP32) from
+ *   a cold start and keeps the fastest for later solves; variant_out (may be NULL)
+ *   receives it, ms_out (may be NULL, 4 floats) the ms per sweep of each variant.
+ *   Untuned precisions use variant 0.  Overwrites the solvers' iterates.
+ * hq_batch_solve: solves every instance cold to opts->tol on Algorithm 1's step
+ *   (opts->tol_kind must be HQ_TOL_STEP; warm starts are not supported); precision,
+ *   check_every, max_sweeps and fp32_stall as for hq_solve (a mixed precision leaves
+ *   FP32 for every instance at once, when all have stalled).  Each check replays one
+ *   captured CUDA graph: [reset step buffers, one cooperative launch of check_every
+ *   sweeps, copy the steps to the host].  Then each solver is finalised as hq_solve does
+ *   (its getters work, its FP64 residual is in stats[c].final_residual).  stats: NULL or
+ *   count entries; ms_total: NULL or the wall time.  Returns HQ_ENOTCONVERGED if some
+ *   instance missed the tolerance, HQ_EDIVERGED, HQ_ETIMEOUT (a bounded device wait gave
+ *   up) or HQ_ECUDA.  Calls on one batch, or on its solvers, must not overlap.
+ * hq_batch_info: out8 = {count, largest N, states swept per sweep (sum of 2^N - 2), work
+ *   items, graph state (1 replayed graph, -1 capture refused and direct launches, 0 not
+ *   tried yet), tuned variant for FP64, DF64, FP32}. */
+typedef struct hq_batch hq_batch;
+int hq_batch_create(hq_solver* const* solvers, int count, void* stream, hq_batch** out);
+int hq_batch_tune(hq_batch* b, int precision, int sweeps, int* variant_out, float* ms_out);
+int hq_batch_solve(hq_batch* b, const hq_opts* opts, hq_stats* stats, double* ms_total);
+int hq_batch_info(const hq_batch* b, int64_t* out8);
+void hq_batch_destroy(hq_batch* b);
+
 void hq_destroy(hq_solver* h);
 const char* hq_strerror(int code);
 const char* hq_last_error(void);

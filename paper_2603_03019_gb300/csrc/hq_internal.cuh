@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/hq.h"
 
@@ -262,6 +263,7 @@ int hq_validate_device(hq_solver* h);
 int hq_build_rates(hq_solver* h);  // r_m in all precisions
 
 // work items and low-part positions of the sweep (hq_items.cu)
+int hq_item_list(int N, std::vector<uint4>& items, int* ifirst);  // host list, layer by layer
 int hq_build_items(hq_solver* h);     // at hq_create, after the layout
 int hq_convert_tables(hq_solver* h);  // at hq_load: FP32 and DF64 copies of the table
 

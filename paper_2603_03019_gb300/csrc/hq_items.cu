@@ -62,16 +62,16 @@ __global__ void k_table_conv(int64_t n, const double* T64, float* T32, float2* T
 
 }  // namespace
 
-int hq_build_items(hq_solver* h) {
+int hq_item_list(int N, std::vector<uint4>& items, int* ifirst) {
   static const HostBinom B;
-  const int N = h->N, L = h->L, H = h->H;
+  const int L = N < HQ_LO_BITS ? N : HQ_LO_BITS, H = N - L;
   if (H > HQ_ITEM_HI_BITS) {
     hq_set_error("item builder: high part too wide");
     return HQ_EINVAL;
   }
-  std::vector<uint4> items;
+  items.clear();
   for (int n = 0; n <= N; n++) {
-    h->ifirst[n] = (int)items.size();
+    ifirst[n] = (int)items.size();
     if (n < 1 || n > N - 1) continue;
     uint64_t expect = 0;  // blocks come in increasing rank order, without gaps
     for (uint32_t hi = 0; hi < (1u << H); hi++) {
@@ -93,13 +93,20 @@ int hq_build_items(hq_solver* h) {
                                    hi | ((uint32_t)w << HQ_ITEM_HI_BITS) | ((uint32_t)(c - 1) << 24), dn, up));
       }
     }
-    if (expect != (uint64_t)h->lsize[n]) {
+    if (expect != (uint64_t)B.c[N][n]) {
       hq_set_error("item builder: rank blocks do not cover the layer");
       return HQ_ECUDA;
     }
   }
-  h->ifirst[N + 1] = (int)items.size();
-  for (int n = N + 2; n < HQ_MAXN + 2; n++) h->ifirst[n] = h->ifirst[N + 1];
+  ifirst[N + 1] = (int)items.size();
+  for (int n = N + 2; n < HQ_MAXN + 2; n++) ifirst[n] = ifirst[N + 1];
+  return HQ_OK;
+}
+
+int hq_build_items(hq_solver* h) {
+  std::vector<uint4> items;
+  const int rc = hq_item_list(h->N, items, h->ifirst);
+  if (rc != HQ_OK) return rc;
   const size_t bytes = sizeof(uint4) * (items.empty() ? 1 : items.size());
   cudaError_t e = cudaMalloc((void**)&h->items, bytes);
   if (e != cudaSuccess) {

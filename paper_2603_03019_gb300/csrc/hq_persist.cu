@@ -43,9 +43,11 @@
 #include <stdlib.h>
 #include <string.h>
 
-#include "hq_internal.cuh"
+#include "hq_sweep_dev.cuh"
 
 namespace {
+
+using namespace hqdev;
 
 constexpr int kThreads = 512;             // 16 warps, two CTAs per SM at 64 registers
 constexpr int kWarps = kThreads / 32;
@@ -55,79 +57,6 @@ constexpr unsigned kSpinLimit = 1u << 24;
 // loads in flight per thread per chunk (busy, idle neighbours), within 64 registers
 template <class V> struct Chunk { static constexpr int b = 2, i = 2; };
 template <> struct Chunk<PolF32> { static constexpr int b = 4, i = 4; };
-
-// ---- PTX helpers ------------------------------------------------------------------------
-__device__ __forceinline__ unsigned long long globaltimer_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-// barrier arrival (acquire + release at gpu scope), release of the barrier, acquire fence
-__device__ __forceinline__ unsigned atom_add_acq_rel(unsigned* p, unsigned v) {
-  unsigned r;
-  asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], %2;" : "=r"(r) : "l"(p), "r"(v) : "memory");
-  return r;
-}
-__device__ __forceinline__ void red_add_release(unsigned* p, unsigned v) {
-  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
-// 16-byte asynchronous global -> shared copy through L2 only (it sees other CTAs' writes
-// made before the grid barrier), and the wait for all of this thread's such copies
-__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
-               "l"(src)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
-// polling load: coherent at gpu scope without the acquire's L1 invalidation, so spinning
-// CTAs do not evict the cached data of CTAs still working on the SM
-__device__ __forceinline__ unsigned ld_relaxed_u32(const unsigned* p) {
-  unsigned v;
-  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
-// ---- loads of values other CTAs wrote in this launch: from L2 (.cg); the table streams
-// through once per sweep (ld_stream, hq_internal.cuh)
-__device__ __forceinline__ double ld_l2(const double* p) { return __ldcg(p); }
-__device__ __forceinline__ float2 ld_l2(const float2* p) { return __ldcg(p); }
-__device__ __forceinline__ float ld_l2(const float* p) { return __ldcg(p); }
-__device__ __forceinline__ double2 ld_l2(const double2* p) { return __ldcg(p); }
-__device__ __forceinline__ float4 ld_l2(const float4* p) { return __ldcg(p); }
-
-// (A, B) pair storage per precision
-template <class V> struct Pair;
-template <> struct Pair<PolF64> {
-  typedef double2 P;
-  __device__ static P pack(double a, double b) { return make_double2(a, b); }
-  __device__ static double A(P p) { return p.x; }
-  __device__ static double B(P p) { return p.y; }
-};
-template <> struct Pair<PolDF> {
-  typedef float4 P;
-  __device__ static P pack(float2 a, float2 b) { return make_float4(a.x, a.y, b.x, b.y); }
-  __device__ static float2 A(P p) { return make_float2(p.x, p.y); }
-  __device__ static float2 B(P p) { return make_float2(p.z, p.w); }
-};
-template <> struct Pair<PolF32> {
-  typedef float2 P;
-  __device__ static P pack(float a, float b) { return make_float2(a, b); }
-  __device__ static float A(P p) { return p.x; }
-  __device__ static float B(P p) { return p.y; }
-};
-
-template <class V>
-__device__ __forceinline__ typename V::T warp_sum(typename V::T v) {
-  for (int m = 16; m > 0; m >>= 1) v = V::add(v, V::shfl_xor(v, m));
-  return v;
-}
-
-// position of the k-th low-part neighbour of a state in its staged block (lidx bytes)
-__device__ __forceinline__ int lo_pos(uint32_t w0, uint32_t w1, uint32_t w2, int k) {
-  const uint32_t wd = k < 4 ? w0 : (k < 8 ? w1 : w2);
-  return (int)((wd >> (8 * (k & 3))) & 0xffu);
-}
 
 struct PersistArgs {
   int N, L, H, nsweeps;
@@ -176,10 +105,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_persist(PersistArgs a) {
   const int N = a.N, L = a.L, H = a.H;
   const unsigned G = gridDim.x;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const uint32_t lmask = (1u << L) - 1u, hmask = (1u << H) - 1u;
-  constexpr int kSlotD = HQ_MAX_BLOCK * (int)sizeof(P2) + 16, kSlotU = HQ_MAX_BLOCK * (int)sizeof(T) + 16;
-  unsigned char* slot_d = smem + (size_t)wid * (kSlotD + kSlotU);
-  unsigned char* slot_u = slot_d + kSlotD;
+  unsigned char* slot_d = smem + (size_t)wid * Slot<V>::kBytes;
+  unsigned char* slot_u = slot_d + Slot<V>::kD;
   for (int i = threadIdx.x; i < (1 << L); i += blockDim.x) s_RL[i] = a.RL[i];
   if (threadIdx.x <= L + 1) {
     // C(L, i - 1): the sizes of the blocks (hi, w -/+ 1) are s_binL[w] and s_binL[w + 2]
@@ -349,129 +276,35 @@ __global__ void __launch_bounds__(kThreads, 2) k_persist(PersistArgs a) {
       if (fin_layer > 0) finalize(fin_layer, ab_prev, md);
       // -- gather layer n -------------------------------------------------------------------
       T sA = V::zero(), sB = V::zero(), sa = V::zero(), sb = V::zero();
-      const int64_t lp = a.lpad[n];
+      LayerView<V> lv;
+      lv.n = n;
+      lv.N = N;
+      lv.L = L;
+      lv.H = H;
+      lv.Sp = a.Sp;
+      lv.off_n = a.off[n];
+      lv.toff_n = a.toff[n];
+      lv.lp = a.lpad[n];
+      lv.masks = a.masks;
+      lv.lidx = a.lidx;
+      lv.RH = a.RH;
+      lv.Tt = Tt;
+      lv.rt = rt;
+      lv.p_up = p_up;
+      lv.ab_prev = ab_prev;
+      lv.ab_cur = ab_cur;
+      lv.nu = s_nu;
+      lv.c1 = s_c1;
+      lv.c2 = s_c2;
+      lv.lamT = s_lamT;
+      lv.one = s_one;
       const int it_end = a.ifirst[n + 1];
       int it = a.ifirst[n] + gwarp;
       uint4 dnext = it < it_end ? __ldg(a.items + it) : make_uint4(0u, 0u, 0u, 0u);
       for (; it < it_end; it += nwarps) {
         const uint4 d = dnext;
         if (it + nwarps < it_end) dnext = __ldg(a.items + it + nwarps);  // next item, ahead
-        const uint32_t rank0 = d.x;
-        const uint32_t hi = d.y & ((1u << HQ_ITEM_HI_BITS) - 1u);
-        const int w = (int)((d.y >> HQ_ITEM_HI_BITS) & 0xfu);
-        const int count = (int)((d.y >> 24) & 0x1fu) + 1;
-        // rank bases of the high-part neighbour blocks: lane j holds RH[hi ^ 2^j][w]
-        const uint32_t hbl = lane < H ? __ldg(a.RH + (size_t)(hi ^ (1u << lane)) * (L + 1) + w) : 0u;
-        // this lane's state (lanes past the item repeat its first state and discard it)
-        const bool act = lane < count;
-        const uint32_t kq = rank0 + (act ? (uint32_t)lane : 0u);
-        const int64_t gi = a.off[n] + kq;
-        const uint32_t x = __ldg(a.masks + gi);
-        const uint32_t iw0 = __ldg(a.lidx + gi), iw1 = __ldg(a.lidx + a.Sp + gi),
-                       iw2 = __ldg(a.lidx + 2 * a.Sp + gi);
-        const T rv = __ldg(rt + gi);
-        const T* tcol = Tt + a.toff[n] + kq;  // table slot s at tcol[s * lp]
-        // stage the low-part neighbour blocks in this warp's slot with 16-byte asynchronous
-        // copies: a block's copy starts at the 16-byte boundary at or below its first
-        // element (offset `dd` / `du` elements into the slot) and covers whole 16-byte units
-        const P2* sdn;
-        const T* sup;
-        {
-          const int dc = (n > 1 && w > 0) ? s_binL[w] : 0;
-          const int uc = w < L ? s_binL[w + 2] : 0;
-          const unsigned char* gd = (const unsigned char*)(ab_prev + d.z);
-          const unsigned char* gu = (const unsigned char*)(p_up + d.w);
-          const int od = (int)((uintptr_t)gd & 15u), ou = (int)((uintptr_t)gu & 15u);
-          const int cd = dc ? (od + dc * (int)sizeof(P2) + 15) >> 4 : 0;
-          const int cu = uc ? (ou + uc * (int)sizeof(T) + 15) >> 4 : 0;
-          for (int c = lane; c < cd; c += 32) cp_async16(slot_d + 16 * c, gd - od + 16 * c);
-          for (int c = lane; c < cu; c += 32) cp_async16(slot_u + 16 * c, gu - ou + 16 * c);
-          cp_async_wait_all();
-          sdn = (const P2*)(slot_d + od);
-          sup = (const T*)(slot_u + ou);
-        }
-        const uint32_t lo = x & lmask;
-        const uint32_t rl = s_RL[lo];
-        __syncwarp();
-        T UA = V::zero(), UB = V::zero(), D = V::zero();
-        // Busy neighbours in table-slot order (increasing unit): w low-part ones from the
-        // staged block, then the high part at rank RH[hi ^ 2^c][w] + RL[lo] of layer n-1.
-        // Idle neighbours, rate nu_u, in increasing unit order: L - w low-part ones from the
-        // staged block, then the high part at rank RH[hi ^ 2^c][w] + RL[lo] of layer n+1.
-        // One chunk takes CB busy and CI idle neighbours, so both chains advance together.
-        {
-          const int nb = n > 1 ? n : 0, ni = N - n, nl = L - w;
-          uint32_t yb = hi, yl = ~lo & lmask, yh = ~hi & hmask;
-          for (int sb0 = 0, si0 = 0; sb0 < nb || si0 < ni; sb0 += CB, si0 += CI) {
-            P2 q[CB];
-            T tv[CB], v[CI];
-            const uint32_t yl0 = yl, yh0 = yh;
-#pragma unroll
-            for (int j = 0; j < CB; j++) {
-              const int s = sb0 + j;
-              if (s < nb) {
-                tv[j] = ld_stream(tcol + s * lp);
-                if (s < w) {
-                  q[j] = sdn[lo_pos(iw0, iw1, iw2, s)];
-                } else {
-                  const int c = __ffs(yb) - 1;
-                  yb &= yb - 1;
-                  q[j] = ld_l2(ab_prev + __shfl_sync(0xffffffffu, hbl, c) + rl);
-                }
-              }
-            }
-#pragma unroll
-            for (int j = 0; j < CI; j++) {
-              const int s = si0 + j;
-              if (s < ni) {
-                if (s < nl) {
-                  yl &= yl - 1;
-                  v[j] = sup[lo_pos(iw0, iw1, iw2, w + s)];
-                } else {
-                  const int c = __ffs(yh) - 1;
-                  yh &= yh - 1;
-                  v[j] = ld_l2(p_up + __shfl_sync(0xffffffffu, hbl, c) + rl);
-                }
-              }
-            }
-#pragma unroll
-            for (int j = 0; j < CB; j++) {
-              if (sb0 + j < nb) {
-                V::fma_acc(UA, PR::A(q[j]), tv[j]);
-                V::fma_acc(UB, PR::B(q[j]), tv[j]);
-              }
-            }
-            uint32_t zl = yl0, zh = yh0;  // replay the unit order for the rates nu_u
-#pragma unroll
-            for (int j = 0; j < CI; j++) {
-              const int s = si0 + j;
-              if (s < ni) {
-                int u;
-                if (s < nl) {
-                  u = __ffs(zl) - 1;
-                  zl &= zl - 1;
-                } else {
-                  u = L + __ffs(zh) - 1;
-                  zh &= zh - 1;
-                }
-                V::fma_acc(D, v[j], s_nu[u]);
-              }
-            }
-          }
-        }
-        // up-inflow: layer 0 is the empty state with p_0 = 1
-        const T U = n == 1 ? ld_stream(tcol)
-                           : V::add(V::mul(s_c1, V::norm(UA)), V::mul(s_c2, V::norm(UB)));
-        D = V::norm(D);
-        const T qm = V::sub(s_one, V::mul(s_lamT, rv));  // mu_m r_m = 1 - lambda r_m
-        const T A = V::mul(U, rv), B = V::mul(D, rv);
-        if (act) {
-          ab_cur[kq] = PR::pack(A, B);
-          sA = V::add(sA, V::mul(U, qm));
-          sB = V::add(sB, V::mul(D, qm));
-          sa = V::add(sa, A);
-          sb = V::add(sb, B);
-        }
+        gather_item<V, CB, CI>(lv, d, s_RL, s_binL, slot_d, slot_u, lane, sA, sB, sa, sb);
         __syncwarp();  // the slot is restaged by the next item
       }
       sync_phase(sA, sB, sa, sb, md, n, n >= 2 ? k : k - 1);
@@ -504,7 +337,7 @@ int launch_persist(hq_solver* h, int nsweeps, cudaEvent_t ev0, cudaEvent_t ev1) 
   typedef typename V::T T;
   typedef typename Pair<V>::P P2;
   const int slot = V::kind == HQ_PREC_FP64 ? 0 : (V::kind == HQ_PREC_DF64 ? 1 : 2);
-  const size_t smem = (size_t)kWarps * (HQ_MAX_BLOCK * (sizeof(P2) + sizeof(T)) + 32);
+  const size_t smem = (size_t)kWarps * Slot<V>::kBytes;
   if (!g_nsm) HQ_CUDA(cudaDeviceGetAttribute(&g_nsm, cudaDevAttrMultiProcessorCount, h->dev));
   if (!g_occ[slot]) {
     HQ_CUDA(cudaFuncSetAttribute(k_persist<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

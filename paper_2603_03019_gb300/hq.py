@@ -78,6 +78,11 @@ _SIGS = {
     "hq_sweep_bytes": (_d, [_vp, _i]),
     "hq_dispatch_table_static": (_i, [_i, _i, _vp, _vp, _vp, _vp]),
     "hq_profile_phases": (_i, [_vp, _vp, _i]),
+    "hq_batch_create": (_i, [_vp, _i, _vp, ctypes.POINTER(_vp)]),
+    "hq_batch_tune": (_i, [_vp, _i, _i, _vp, _vp]),
+    "hq_batch_solve": (_i, [_vp, ctypes.POINTER(hq_opts), _vp, _vp]),
+    "hq_batch_info": (_i, [_vp, _vp]),
+    "hq_batch_destroy": (None, [_vp]),
 }
 
 
@@ -233,6 +238,43 @@ def hq_dispatch_table_static(N: int, J: int, lambda_j, pref, T, stream=None) -> 
 def hq_destroy(h: int) -> None:
     if h:
         load().hq_destroy(h)
+
+
+def hq_batch_create(handles, stream=None) -> int:
+    arr = (_vp * len(handles))(*handles)
+    b = _vp()
+    s = stream if isinstance(stream, int) or stream is None else stream.cuda_stream
+    _check(load().hq_batch_create(arr, len(handles), s, ctypes.byref(b)))
+    return b.value
+
+
+def hq_batch_tune(b: int, precision: int, sweeps: int = 4) -> tuple[int, np.ndarray]:
+    ms = np.zeros(4, dtype=np.float32)
+    v = ctypes.c_int(0)
+    _check(load().hq_batch_tune(b, precision, sweeps, ctypes.addressof(v), ms.ctypes.data))
+    return v.value, ms
+
+
+def hq_batch_solve(b: int, count: int, opts: hq_opts | None = None,
+                   allow_notconverged: bool = True) -> tuple[int, list, float]:
+    st = (hq_stats * count)()
+    ms = np.zeros(1)
+    allow = (HQ_OK, HQ_ENOTCONVERGED) if allow_notconverged else (HQ_OK,)
+    rc = load().hq_batch_solve(b, ctypes.byref(opts) if opts is not None else None,
+                               ctypes.addressof(st), ms.ctypes.data)
+    _check(rc, allow)
+    return rc, [st[i].as_dict() for i in range(count)], float(ms[0])
+
+
+def hq_batch_info(b: int) -> np.ndarray:
+    out = np.zeros(8, dtype=np.int64)
+    _check(load().hq_batch_info(b, out.ctypes.data))
+    return out
+
+
+def hq_batch_destroy(b: int) -> None:
+    if b:
+        load().hq_batch_destroy(b)
 
 
 def hq_launch_count(reset: bool = False) -> int:
