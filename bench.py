@@ -65,6 +65,10 @@ def parse():
     ap.add_argument("--no-compare", action="store_true", help="skip the per-precision comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--batch", type=int, default=0, metavar="K",
+                    help="batched workload: K deployments, N ~ U{12..18}, J=200 (one JSON line)")
+    ap.add_argument("--warmstart", action="store_true",
+                    help="learned warm start vs cold start on held-out N=16..22 instances (one JSON line)")
     ap.add_argument("--profile", action="store_true",
                     help="one instance load and `--sweeps` DF64 sweeps, nothing else (for ncu)")
     ap.add_argument("--sweeps", type=int, default=2)
@@ -415,8 +419,131 @@ def run_ours(args):
     return 0
 
 
+def run_batch(args):
+    """K deployments with N drawn from 12..18 solved by the batched solver (one persistent
+    launch per check, replayed from a captured graph, kernel variant from the autotuner)
+    against the same instances solved one at a time with the same options."""
+    import torch
+
+    from paper_2603_03019_gb300 import hq
+
+    hq.load()
+    K = args.batch
+    insts = I.batch_n12_18(count=K)
+    stream = torch.cuda.Stream()
+    solvers = [hq.Solver.for_instance(i, stream=stream) for i in insts]
+    b = hq.hq_batch_create([s.h for s in solvers], stream=stream)
+    prec = hq.PRECISION[args.precision]
+    tuned = {}
+    for name, pc in (("fp32", hq.HQ_PREC_FP32), ("df64", hq.HQ_PREC_DF64), ("fp64", hq.HQ_PREC_FP64)):
+        v, ms = hq.hq_batch_tune(b, pc, 4)
+        tuned[name] = {"variant": v, "ms_per_sweep": [round(float(x), 4) for x in ms]}
+
+    def opts():
+        o = hq.hq_default_opts()
+        o.tol = args.tol
+        o.tol_kind = hq.HQ_TOL_STEP
+        o.precision = prec
+        o.check_every = 8
+        return o
+
+    for _ in range(max(1, args.warmup)):
+        hq.hq_batch_solve(b, K, opts())
+    times, sweeps = [], []
+    for _ in range(args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rc, stats, _ = hq.hq_batch_solve(b, K, opts())
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+        sweeps.append(sum(((1 << i.N) - 2) * (st["sweeps_fp32"] + st["sweeps_hi"])
+                          for i, st in zip(insts, stats)))
+    t_batch = min(times)
+    upd = sweeps[times.index(t_batch)]
+    conv = sum(st["converged"] for st in stats)
+    info = hq.hq_batch_info(b)
+    hq.hq_batch_destroy(b)
+    # one at a time, same options (step tolerance), same GPU
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    upd1 = 0.0
+    for s in solvers:
+        o = opts()
+        rc1, st1 = hq.hq_solve(s.h, o)
+        upd1 += st1.state_updates
+    torch.cuda.synchronize()
+    t_one = time.perf_counter() - t0
+    for s in solvers:
+        s.close()
+    line = {
+        "metric": "batched solves: instances solved per second (N ~ U{12..18}, J=200, loss, "
+                  "step tolerance), one persistent launch per check under a captured graph",
+        "value": K / t_batch, "unit": "instances/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1000 * t_batch, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+        "config": {"workload": f"batch{K}_n12_18_j200", "instances": K, "largest_N": int(info[1]),
+                   "states": int(info[2]), "tol_step": args.tol, "precision": args.precision},
+        "state_updates_per_s": upd / t_batch, "converged": conv,
+        "graph": {1: "captured graph replayed", -1: "capture refused: direct launches",
+                  0: "not run"}[int(info[4])],
+        "autotuner": tuned,
+        "one_at_a_time": {"seconds": t_one, "instances_per_s": K / t_one,
+                          "state_updates_per_s": upd1 / t_one},
+        "speedup_vs_one_at_a_time": t_one / t_batch,
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def run_warmstart(args):
+    """Held-out instances (seeds never used in training), N = 16..22, J = 300: sweeps and
+    wall time to a 1e-10 relative balance residual from the paper's uniform start and
+    from the learned start (with its fallback), same solver, same GPU."""
+    import torch
+
+    from paper_2603_03019_gb300 import hq
+
+    hq.load()
+    m = hq.load_warmstart_model()
+    rows = []
+    for N in (16, 18, 20, 22):
+        for k in range(2):
+            inst = I.warmstart_instance(880_000 + 10 * N + k, N=N, J=300)
+            s = hq.Solver.for_instance(inst)
+            hq.hq_attach_mlp(s.h, m)
+            res = {}
+            for name, warm in (("cold", False), ("learned", True)):
+                s.solve(tol=args.tol, precision=args.precision, warm_mlp=warm)  # warm-up
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                rc, st = s.solve(tol=args.tol, precision=args.precision, warm_mlp=warm)
+                torch.cuda.synchronize()
+                res[name] = {"ms": 1000 * (time.perf_counter() - t0),
+                             "sweeps": st["sweeps_fp32"] + st["sweeps_hi"],
+                             "residual": st["final_residual"], "warm_used": st["warm_used"]}
+            rows.append({"N": N, "seed": 880_000 + 10 * N + k, **res})
+            s.close()
+    hq.hq_mlp_destroy(m)
+    cold = sum(r["cold"]["ms"] for r in rows)
+    warm = sum(r["learned"]["ms"] for r in rows)
+    line = {"metric": "time to 1e-10 residual, learned warm start vs cold start (held-out N=16..22)",
+            "value": cold / warm, "unit": "speedup (cold time / learned time)", "n_gpus": 1,
+            "higher_is_better": True, "data": "synthetic", "dtype": args.precision,
+            "config": {"workload": "warmstart_heldout_n16_22_j300", "instances": len(rows),
+                       "precision": args.precision, "tol": args.tol},
+            "sweeps_cold": sum(r["cold"]["sweeps"] for r in rows),
+            "sweeps_learned": sum(r["learned"]["sweeps"] for r in rows),
+            "rows": rows}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse()
+    if args.warmstart:
+        return run_warmstart(args)
+    if args.batch:
+        return run_batch(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.profile:

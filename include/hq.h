@@ -244,6 +244,55 @@ int hq_batch_solve(hq_batch* b, const hq_opts* opts, hq_stats* stats, double* ms
 int hq_batch_info(const hq_batch* b, int64_t* out8);
 void hq_batch_destroy(hq_batch* b);
 
+/* ---- learned warm start ---------------------------------------------------------------
+ * Not in the paper (which starts Algorithm 1 from p_n = 1/C(N,n), Sec. 3.2).  A small
+ * network predicts, for every layer n = 1..N-1 and unit i, the conditional occupancy
+ * q_i(n) = P(unit i busy | n units busy) from 9 inputs (hq_mlp_features): the unit's
+ * nu_i / mean nu, the demand shares of the nodes ranking it first, second and third,
+ * lambda s1_i / nu_i, lambda / sum nu, log(nu_i / mean nu), N / 16, and n / N.  hq_solve
+ * with warm_start = HQ_WARM_MLP then starts from the layer-wise product form
+ * p_n(B) = prod_{i in B} x_i(n) / e_n(x(n)), x_i(n) = q_i(n) / (1 - q_i(n)), and keeps it
+ * only if its first sweep's step is no larger than that of a first sweep from the uniform
+ * start (both probe sweeps are counted in the stats; stats.warm_used says which won).
+ *
+ * Network, weights shared across units and layers: 9 -> hidden (ReLU) -> hidden (ReLU)
+ * -> 1, the output estimating logit(q_i(n)); activations stored in BF16, the hidden x
+ * hidden product on BF16 tensor cores with FP32 accumulation, master weights FP32.
+ * Parameter order of the flat FP32 vector: W1 [9 x hidden] row-major, b1 [hidden],
+ * W2 [hidden x hidden] row-major (input index first), b2 [hidden], W3 [hidden], b3 [1].
+ *
+ * hq_mlp_create: hidden a multiple of 16 in 16..4096; He-uniform weights from a
+ *   splitmix64 stream seeded by `seed`, zero biases; stream as for hq_create.
+ * hq_mlp_set_weights / _get_weights: n must equal hq_mlp_num_params; mem: HQ_HOST or
+ *   HQ_DEVICE; setting resets the optimiser state.
+ * hq_mlp_forward: X (B x 9 FP32, device), y (B FP32, device).
+ * hq_mlp_gradients: loss = mean (y - target)^2 over the B rows and its gradient with
+ *   respect to the flat parameters into grad (device, num_params FP32; may be NULL);
+ *   loss (host float, may be NULL).  X and target: device memory.
+ * hq_mlp_train_step: the same gradient, then one Adam step (beta 0.9 / 0.999, eps 1e-8)
+ *   with learning rate lr > 0.
+ * hq_mlp_features: the network inputs of a loaded solver (N >= 2), one row per (layer
+ *   n = 1..N-1, unit i), row (n-1) N + i, N (N-1) x 9 FP32, host or device per mem.
+ * hq_mlp_predict: for a loaded solver, q ((N+1) x N doubles, row n = q_(.)(n), rows 0 and
+ *   N exact), the layer law P(n) of the loss system with lambda(n) = lambda and
+ *   mu(n) = sum_i nu_i q_i(n) (Eq. 10; N+1 doubles, may be NULL) and
+ *   rho_i = sum_n P(n) q_i(n) (N doubles, may be NULL), all in the memory given by mem.
+ * hq_attach_mlp: borrow a model for HQ_WARM_MLP solves of this solver (NULL detaches).
+ * Errors: HQ_EINVAL for NULL or inconsistent arguments, HQ_ESTATE if not loaded,
+ * HQ_ENOMEM, HQ_ECUDA. */
+typedef struct hq_mlp hq_mlp;
+int hq_mlp_create(int hidden, uint64_t seed, void* stream, hq_mlp** out);
+int64_t hq_mlp_num_params(const hq_mlp* m);
+int hq_mlp_set_weights(hq_mlp* m, const float* w, int64_t n, int mem);
+int hq_mlp_get_weights(hq_mlp* m, float* w, int64_t n, int mem);
+int hq_mlp_forward(hq_mlp* m, const float* X, int B, float* y);
+int hq_mlp_gradients(hq_mlp* m, const float* X, const float* target, int B, float* grad, float* loss);
+int hq_mlp_train_step(hq_mlp* m, const float* X, const float* target, int B, float lr, float* loss);
+int hq_mlp_features(hq_solver* h, float* X, int mem);
+int hq_mlp_predict(hq_solver* h, hq_mlp* m, double* q, double* pn, double* rho, int mem);
+int hq_attach_mlp(hq_solver* h, hq_mlp* m);
+void hq_mlp_destroy(hq_mlp* m);
+
 void hq_destroy(hq_solver* h);
 const char* hq_strerror(int code);
 const char* hq_last_error(void);

@@ -59,7 +59,7 @@ extern "C" void hq_default_opts(hq_opts* o) {
 
 static void free_all(hq_solver* h) {
   void* ptrs[] = {h->masks, h->RL, h->RH, h->lam_j, h->nu, h->pref, h->pre, h->zeta,
-                  h->lidx, h->items,
+                  h->lidx, h->items, h->wfeat, h->wy, h->wlx,
                   h->b64.T, h->b64.r, h->b64.p, h->b64.nu, h->bdf.T, h->bdf.r, h->bdf.p, h->bdf.nu,
                   h->b32.T, h->b32.r, h->b32.p, h->b32.nu, h->ab, h->partials, h->sc, h->dflag,
                   h->P, h->pn, h->rho, h->R, h->W, h->summary, h->pcond};
@@ -154,6 +154,9 @@ extern "C" int hq_create(int N, int J, int mode, int capacity_C, void* stream, h
   HQ_TRY(dalloc(h, (float2**)&h->bdf.T, TE * 8));
   HQ_TRY(dalloc(h, (float**)&h->b32.T, TE * 4));
   HQ_TRY(dalloc(h, &h->lidx, SP * 12));
+  HQ_TRY(dalloc(h, &h->wfeat, (int64_t)HQ_MAXN * HQ_MAXN * HQ_MLP_FEATURES * 4));
+  HQ_TRY(dalloc(h, &h->wy, (int64_t)HQ_MAXN * HQ_MAXN * 4));
+  HQ_TRY(dalloc(h, &h->wlx, ((int64_t)HQ_MAXN * HQ_MAXN + HQ_MAXN + 1) * 8));
   HQ_TRY(dalloc(h, (double**)&h->b64.r, SP * 8));
   HQ_TRY(dalloc(h, (float2**)&h->bdf.r, SP * 8));
   HQ_TRY(dalloc(h, (float**)&h->b32.r, SP * 4));
@@ -276,7 +279,7 @@ extern "C" int hq_solve(hq_solver* h, const hq_opts* opts_in, hq_stats* stats) {
   if (o.precision < HQ_PREC_FP64 || o.precision > HQ_PREC_FP32_FP64) { hq_set_error("bad precision"); return HQ_EINVAL; }
   if (o.tol_kind != HQ_TOL_STEP && o.tol_kind != HQ_TOL_RESIDUAL) { hq_set_error("bad tol_kind"); return HQ_EINVAL; }
   if (o.warm_start == HQ_WARM_GIVEN && !o.warm_p) { hq_set_error("warm_p is NULL"); return HQ_EINVAL; }
-  if (o.warm_start == HQ_WARM_MLP) { hq_set_error("no warm-start model is attached"); return HQ_EINVAL; }
+  if (o.warm_start == HQ_WARM_MLP && !h->mlp) { hq_set_error("no warm-start model is attached"); return HQ_EINVAL; }
   double stall = o.fp32_stall > 0.0 ? o.fp32_stall : 0.9;
   auto t0 = std::chrono::steady_clock::now();
 
@@ -290,13 +293,37 @@ extern "C" int hq_solve(hq_solver* h, const hq_opts* opts_in, hq_stats* stats) {
     default: phases[0] = HQ_PREC_FP32; phases[1] = HQ_PREC_FP64; nph = 2; break;
   }
   int ph = 0;
-  int rc = hq_init_iterate(h, phases[0], o.warm_start == HQ_WARM_GIVEN ? o.warm_p : nullptr,
-                           o.warm_mem);
-  if (rc != HQ_OK) return rc;
-  h->solved = false;
-
   int sweeps[2] = {0, 0};
   int total = 0, checks = 0, res_checks = 0, since_res = 0, stalled = 0;
+  bool warm_kept = o.warm_start == HQ_WARM_GIVEN;
+  int rc;
+  if (o.warm_start == HQ_WARM_MLP && h->N >= 2) {
+    // the learned start is kept only if its first sweep moves the iterate no more than
+    // a first sweep from the paper's uniform start does; both probe sweeps are counted
+    rc = hq_init_iterate(h, phases[0], nullptr, HQ_HOST);
+    if (rc == HQ_OK) rc = hq_run_sweeps(h, phases[0], 1, nullptr, nullptr);
+    if (rc == HQ_OK) rc = pull_scalars(h);
+    if (rc != HQ_OK) return rc;
+    const double step_cold = h->hsc->step;
+    rc = hq_mlp_warm_start(h, h->mlp, h->pcond, nullptr);
+    if (rc == HQ_OK) rc = hq_init_iterate(h, phases[0], h->pcond, HQ_DEVICE);
+    if (rc == HQ_OK) rc = hq_run_sweeps(h, phases[0], 1, nullptr, nullptr);
+    if (rc == HQ_OK) rc = pull_scalars(h);
+    if (rc != HQ_OK) return rc;
+    const double step_warm = h->hsc->step;
+    sweeps[phases[0] == HQ_PREC_FP32 ? 0 : 1] += 2;
+    total = 2;
+    warm_kept = isfinite(step_warm) && step_warm <= step_cold;
+    if (!warm_kept) {
+      rc = hq_init_iterate(h, phases[0], nullptr, HQ_HOST);
+      if (rc != HQ_OK) return rc;
+    }
+  } else {
+    rc = hq_init_iterate(h, phases[0], o.warm_start == HQ_WARM_GIVEN ? o.warm_p : nullptr, o.warm_mem);
+    if (rc != HQ_OK) return rc;
+  }
+  h->solved = false;
+
   double step = INFINITY, prev_check_step = 0.0;
   double res = -1.0, res_at_step = 0.0;
   bool converged = false;
@@ -394,7 +421,7 @@ extern "C" int hq_solve(hq_solver* h, const hq_opts* opts_in, hq_stats* stats) {
     stats->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     stats->ms_table = h->ms_table;
     stats->state_updates = (double)(h->S - 2) * (double)total;
-    stats->warm_used = o.warm_start != HQ_WARM_NONE ? 1 : 0;
+    stats->warm_used = warm_kept ? 1 : 0;
   }
   (void)checks;
   return status;

@@ -24,6 +24,8 @@
 // states of one block, processed by one warp: uint4 {rank0, hi | w << 20 | (count-1) << 24,
 // rank of block (hi, w-1) in layer n-1, rank of block (hi, w+1) in layer n+1}.
 #define HQ_ITEM_HI_BITS 20
+#define HQ_MLP_UNIT_FEATURES 8  // per-unit features of an instance
+#define HQ_MLP_FEATURES 9       // inputs of the warm-start network: unit features + n / N
 #define HQ_MAX_BLOCK 252   // C(HQ_LO_BITS, HQ_LO_BITS / 2)
 
 // ---------------------------------------------------------------------------
@@ -250,6 +252,11 @@ struct hq_solver {
   double* summary = nullptr;   // 8
   double* pcond = nullptr;     // S, y-order conditional (normalised)
   double ms_table = 0;
+  // learned warm start: attached model (borrowed) and scratch
+  hq_mlp* mlp = nullptr;
+  float* wfeat = nullptr;      // N (N-1) rows x HQ_MLP_FEATURES: (layer n, unit i) pairs
+  float* wy = nullptr;         // N (N-1) predictions (logit q_i(n))
+  double* wlx = nullptr;       // log x_i(n) [HQ_MAXN^2], log e_n [HQ_MAXN + 1]
 };
 
 // ---------------------------------------------------------------------------
@@ -261,6 +268,11 @@ double hq_binom(int n, int k);
 int hq_build_layout(hq_solver* h);
 int hq_validate_device(hq_solver* h);
 int hq_build_rates(hq_solver* h);  // r_m in all precisions
+
+// learned warm start (hq_mlp.cu)
+int hq_mlp_predict_dev(hq_mlp* m, const float* X, int B, float* y_dev, cudaStream_t s);
+int hq_mlp_features_dev(hq_solver* h, float* X);
+int hq_mlp_warm_start(hq_solver* h, hq_mlp* m, double* P, double* rho);
 
 // work items and low-part positions of the sweep (hq_items.cu)
 int hq_item_list(int N, std::vector<uint4>& items, int* ifirst);  // host list, layer by layer

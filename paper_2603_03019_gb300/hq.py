@@ -8,6 +8,7 @@ library cannot be built or loaded, ``load()`` raises.
 from __future__ import annotations
 
 import ctypes
+import os
 import threading
 
 import numpy as np
@@ -83,6 +84,17 @@ _SIGS = {
     "hq_batch_solve": (_i, [_vp, ctypes.POINTER(hq_opts), _vp, _vp]),
     "hq_batch_info": (_i, [_vp, _vp]),
     "hq_batch_destroy": (None, [_vp]),
+    "hq_mlp_create": (_i, [_i, ctypes.c_uint64, _vp, ctypes.POINTER(_vp)]),
+    "hq_mlp_num_params": (ctypes.c_int64, [_vp]),
+    "hq_mlp_set_weights": (_i, [_vp, _vp, ctypes.c_int64, _i]),
+    "hq_mlp_get_weights": (_i, [_vp, _vp, ctypes.c_int64, _i]),
+    "hq_mlp_forward": (_i, [_vp, _vp, _i, _vp]),
+    "hq_mlp_gradients": (_i, [_vp, _vp, _vp, _i, _vp, _vp]),
+    "hq_mlp_train_step": (_i, [_vp, _vp, _vp, _i, ctypes.c_float, _vp]),
+    "hq_mlp_features": (_i, [_vp, _vp, _i]),
+    "hq_mlp_predict": (_i, [_vp, _vp, _vp, _vp, _vp, _i]),
+    "hq_attach_mlp": (_i, [_vp, _vp]),
+    "hq_mlp_destroy": (None, [_vp]),
 }
 
 
@@ -277,6 +289,92 @@ def hq_batch_destroy(b: int) -> None:
         load().hq_batch_destroy(b)
 
 
+def hq_mlp_create(hidden: int = 256, seed: int = 1, stream=None) -> int:
+    m = _vp()
+    s = stream if isinstance(stream, int) or stream is None else stream.cuda_stream
+    _check(load().hq_mlp_create(hidden, seed, s, ctypes.byref(m)))
+    return m.value
+
+
+def hq_mlp_num_params(m: int) -> int:
+    return int(load().hq_mlp_num_params(m))
+
+
+def hq_mlp_set_weights(m: int, w) -> None:
+    p, mem = _ptr(w)
+    _check(load().hq_mlp_set_weights(m, p, hq_mlp_num_params(m), mem))
+
+
+def hq_mlp_get_weights(m: int, out=None):
+    if out is None:
+        out = np.empty(hq_mlp_num_params(m), dtype=np.float32)
+    p, mem = _ptr(out)
+    _check(load().hq_mlp_get_weights(m, p, hq_mlp_num_params(m), mem))
+    return out
+
+
+def hq_mlp_forward(m: int, X, y) -> None:
+    """X: (B, 8) float32 CUDA tensor; y: (B,) float32 CUDA tensor."""
+    _check(load().hq_mlp_forward(m, X.data_ptr(), X.shape[0], y.data_ptr()))
+
+
+def hq_mlp_gradients(m: int, X, target, grad=None) -> float:
+    loss = ctypes.c_float(0.0)
+    _check(load().hq_mlp_gradients(m, X.data_ptr(), target.data_ptr(), X.shape[0],
+                                   grad.data_ptr() if grad is not None else None,
+                                   ctypes.addressof(loss)))
+    return float(loss.value)
+
+
+def hq_mlp_train_step(m: int, X, target, lr: float, want_loss: bool = True):
+    loss = ctypes.c_float(0.0)
+    _check(load().hq_mlp_train_step(m, X.data_ptr(), target.data_ptr(), X.shape[0], lr,
+                                    ctypes.addressof(loss) if want_loss else None))
+    return float(loss.value) if want_loss else None
+
+
+def hq_mlp_features(h: int, out=None, N: int | None = None):
+    """Network inputs, one row per (layer n = 1..N-1, unit i): (N (N-1), 9) float32."""
+    if out is None:
+        out = np.empty((N * (N - 1), 9), dtype=np.float32)
+    p, mem = _ptr(out)
+    _check(load().hq_mlp_features(h, p, mem))
+    return out
+
+
+def hq_mlp_predict(h: int, m: int, N: int) -> tuple[np.ndarray, np.ndarray, np.ndarray]:
+    """(q (N+1, N), layer law P(n), rho) of the model for the loaded instance."""
+    q = np.empty((N + 1, N))
+    pn = np.empty(N + 1)
+    rho = np.empty(N)
+    _check(load().hq_mlp_predict(h, m, q.ctypes.data, pn.ctypes.data, rho.ctypes.data, HQ_HOST))
+    return q, pn, rho
+
+
+def hq_attach_mlp(h: int, m: int | None) -> None:
+    _check(load().hq_attach_mlp(h, m))
+
+
+def hq_mlp_destroy(m: int) -> None:
+    if m:
+        load().hq_mlp_destroy(m)
+
+
+WARMSTART_WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "data",
+                                 "warmstart_mlp_h256.f32")
+
+
+def load_warmstart_model(path: str = WARMSTART_WEIGHTS, hidden: int = 256) -> int:
+    """A model handle with the weights trained by train_warmstart.py (raw float32 file)."""
+    w = np.fromfile(path, dtype="<f4")
+    m = hq_mlp_create(hidden, 1)
+    if w.size != hq_mlp_num_params(m):
+        hq_mlp_destroy(m)
+        raise ValueError(f"{path}: {w.size} parameters, the network has {hq_mlp_num_params(m)}")
+    hq_mlp_set_weights(m, np.ascontiguousarray(w))
+    return m
+
+
 def hq_launch_count(reset: bool = False) -> int:
     return int(load().hq_launch_count(1 if reset else 0))
 
@@ -304,7 +402,7 @@ class Solver:
         hq_load(self.h, lam_j, nu, pref)
 
     def solve(self, tol=1e-10, tol_kind=HQ_TOL_RESIDUAL, precision="fp32+df64", max_sweeps=100000,
-              check_every=8, warm_p=None, fp32_stall=0.0) -> tuple[int, dict]:
+              check_every=8, warm_p=None, fp32_stall=0.0, warm_mlp=False) -> tuple[int, dict]:
         o = hq_default_opts()
         o.tol = tol
         o.tol_kind = tol_kind
@@ -320,6 +418,8 @@ class Solver:
             o.warm_start = HQ_WARM_GIVEN
             o.warm_p = p
             o.warm_mem = m
+        elif warm_mlp:
+            o.warm_start = HQ_WARM_MLP
         rc, st = hq_solve(self.h, o)
         del keep
         return rc, st.as_dict()
