@@ -62,6 +62,9 @@ def parse():
     ap.add_argument("--workload", default="n24", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="fp32+df64")
     ap.add_argument("--tol", type=float, default=1e-10)
+    ap.add_argument("--omega", type=float, default=-1.0,
+                    help="over-relaxation of the outer iteration: 1 = Algorithm 1 as printed, "
+                         "negative = automatic (default)")
     ap.add_argument("--no-compare", action="store_true", help="skip the per-precision comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
@@ -256,12 +259,13 @@ def run_ours(args):
     solver = hq.Solver(N, J, inst.mode, inst.C, stream=stream)
     prec = hq.PRECISION[args.precision]
 
-    def opts(precision=prec, tol=args.tol):
+    def opts(precision=prec, tol=args.tol, omega=args.omega):
         o = hq.hq_default_opts()
         o.tol = tol
         o.tol_kind = hq.HQ_TOL_RESIDUAL
         o.precision = precision
         o.check_every = 8
+        o.omega = omega
         return o
 
     def step_device():
@@ -346,11 +350,13 @@ def run_ours(args):
         compare = {}
         if not args.no_compare and rank == 0:
             hq.hq_load(solver.h, lam_d, nu_d, pref_d)
-            for name in ("fp64", "df64", "fp32+df64"):
-                rc, st = hq.hq_solve(solver.h, opts(hq.PRECISION[name]))
+            runs = (("fp64", "fp64", 1.0), ("df64", "df64", 1.0), ("fp32+df64", "fp32+df64", 1.0),
+                    ("fp64+sor", "fp64", -1.0), ("fp32+df64+sor", "fp32+df64", -1.0))
+            for name, pname, om in runs:
+                rc, st = hq.hq_solve(solver.h, opts(hq.PRECISION[pname], omega=om))
                 compare[name] = {"ms": round(st.ms_total, 3), "sweeps_fp32": st.sweeps_fp32,
                                  "sweeps_hi": st.sweeps_hi, "residual": st.final_residual,
-                                 "converged": bool(st.converged)}
+                                 "omega": round(st.omega, 3), "converged": bool(st.converged)}
             if "fp64" in compare and compare["fp64"]["ms"] > 0:
                 for name in compare:
                     compare[name]["speedup_vs_fp64"] = round(compare["fp64"]["ms"] / compare[name]["ms"], 3)
@@ -403,6 +409,7 @@ def run_ours(args):
         "data": "synthetic",
         "config": {"workload": inst.name, "N": N, "J": J, "mode": I.MODE_NAMES[inst.mode],
                    "load": round(inst.load, 4), "tol": args.tol, "precision": args.precision,
+                   "omega": "automatic" if args.omega < 0 else args.omega,
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                    "l2": "inputs larger than L2 (DF64 table 1.6 GB, FP32 table 0.8 GB)"},
         "sweeps_per_step": {"fp32": st0["sweeps_fp32"], "hi": st0["sweeps_hi"]},

@@ -82,7 +82,14 @@ typedef struct hq_opts {
   const double* warm_p;/* HQ_WARM_GIVEN: start vector p_n(B) in y-order, length 2^N */
   double fp32_stall;   /* mixed modes: leave FP32 when the step's decay per check is
                           worse than this ratio (0 = default 0.9) */
-  int reserved[6];
+  double omega;        /* over-relaxation of the outer iteration (not in the paper):
+                          each finalised layer becomes p_old + omega (p_new - p_old);
+                          0 or 1 = Algorithm 1 as printed; (1, 2) fixed; negative =
+                          automatic (Young's optimal omega for the contraction rate
+                          observed over the first checks, 90 % of it, at most 1.5,
+                          backed off when the steps stop shrinking).  The fixed point
+                          is the same for any omega. */
+  int reserved[4];
 } hq_opts;
 
 typedef struct hq_stats {
@@ -96,7 +103,9 @@ typedef struct hq_stats {
   double ms_table;        /* wall time of the table build in the last hq_load */
   double state_updates;   /* (2^N - 2) * total sweeps */
   int warm_used;          /* 1 if a warm start was kept, 0 if cold (or fell back) */
-  int reserved[5];
+  int pad0;
+  double omega;           /* over-relaxation in use at the end of the solve */
+  int reserved[2];
 } hq_stats;
 
 typedef struct hq_solver hq_solver;

@@ -55,6 +55,7 @@ extern "C" void hq_default_opts(hq_opts* o) {
   o->warm_mem = HQ_HOST;
   o->warm_p = nullptr;
   o->fp32_stall = 0.9;
+  o->omega = 1.0;
 }
 
 static void free_all(hq_solver* h) {
@@ -281,6 +282,13 @@ extern "C" int hq_solve(hq_solver* h, const hq_opts* opts_in, hq_stats* stats) {
   if (o.warm_start == HQ_WARM_GIVEN && !o.warm_p) { hq_set_error("warm_p is NULL"); return HQ_EINVAL; }
   if (o.warm_start == HQ_WARM_MLP && !h->mlp) { hq_set_error("no warm-start model is attached"); return HQ_EINVAL; }
   double stall = o.fp32_stall > 0.0 ? o.fp32_stall : 0.9;
+  if (!(o.omega < 2.0) || (o.omega >= 0.0 && o.omega < 1.0 && o.omega != 0.0)) {
+    hq_set_error("omega must be 0, in [1, 2), or negative (automatic)");
+    return HQ_EINVAL;
+  }
+  const bool auto_omega = o.omega < 0.0;
+  h->omega = o.omega >= 1.0 ? o.omega : 1.0;
+  int omega_checks = 0;
   auto t0 = std::chrono::steady_clock::now();
 
   int phases[2];
@@ -355,6 +363,20 @@ extern "C" int hq_solve(hq_solver* h, const hq_opts* opts_in, hq_stats* stats) {
       break;
     }
     const double ratio = prev_check_step > 0.0 ? step / prev_check_step : 0.0;
+    if (auto_omega) {
+      // Young's optimal relaxation for the observed contraction: with Algorithm 1's
+      // per-sweep rate r (measured over the third check, past the start's transient),
+      // omega_opt = 2 / (1 + sqrt(1 - r)); take 90 % of its extrapolation, at most 1.5,
+      // and back off halfway whenever the steps stop shrinking
+      omega_checks++;
+      if (h->omega == 1.0 && omega_checks == 3 && ratio > 0.0 && ratio < 1.0) {
+        const double r = pow(ratio, 1.0 / nrun);
+        const double wopt = 2.0 / (1.0 + sqrt(1.0 - r));
+        h->omega = fmin(1.0 + 0.9 * (wopt - 1.0), 1.5);
+      } else if (h->omega > 1.0 && ratio >= 1.0) {
+        h->omega = 1.0 + 0.5 * (h->omega - 1.0);
+      }
+    }
     const bool last_phase = ph == nph - 1;
     if (!last_phase) {
       // leave FP32 once its steps stop shrinking geometrically (rounding floor)
@@ -422,6 +444,7 @@ extern "C" int hq_solve(hq_solver* h, const hq_opts* opts_in, hq_stats* stats) {
     stats->ms_table = h->ms_table;
     stats->state_updates = (double)(h->S - 2) * (double)total;
     stats->warm_used = warm_kept ? 1 : 0;
+    stats->omega = h->omega;
   }
   (void)checks;
   return status;

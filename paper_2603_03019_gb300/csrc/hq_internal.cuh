@@ -222,6 +222,7 @@ struct hq_solver {
   double lam = 0, nu_sum = 0;
   bool loaded = false, solved = false;
   int cur_prec = -1;           // precision holding the current iterate
+  double omega = 1.0;          // over-relaxation of the finalised layers (1: Algorithm 1)
 
   // N-dependent layout
   uint32_t* masks = nullptr;   // S, layer-ranked state masks

@@ -61,6 +61,7 @@ template <> struct Chunk<PolF32> { static constexpr int b = 4, i = 4; };
 struct PersistArgs {
   int N, L, H, nsweeps;
   double lam;
+  double omega;                 // over-relaxation of the finalised layers (1: none)
   int64_t Sp;
   int64_t off[HQ_MAXN + 2];     // padded per-state offsets of the layers
   int64_t toff[HQ_MAXN + 2];    // padded table offsets of the layers
@@ -147,6 +148,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_persist(PersistArgs a) {
   // finalise layer lf from the (A, B) buffer `abf`: p = c1 A + c2 B, |p - p_old|
   auto finalize = [&](int lf, const P2* abf, float& md) {
     const T c1 = s_c1, c2 = s_c2;
+    const bool relax = a.omega != 1.0;
+    const T om = V::from_d(a.omega);
     T* pl = pw + a.off[lf];
     const int64_t Lf = a.lsize[lf];
     const int64_t nthreads = (int64_t)G * blockDim.x;
@@ -154,7 +157,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_persist(PersistArgs a) {
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < Lf; k += nthreads) {
       const P2 q = ld_l2(abf + k);
       const T old = ld_l2(pl + k);
-      const T v = V::add(V::mul(c1, PR::A(q)), V::mul(c2, PR::B(q)));
+      T v = V::add(V::mul(c1, PR::A(q)), V::mul(c2, PR::B(q)));
+      if (relax) v = V::add(old, V::mul(om, V::sub(v, old)));
       md = fmaxf(md, V::absdiff(v, old));
       pl[k] = v;
     }
@@ -366,6 +370,7 @@ int launch_persist(hq_solver* h, int nsweeps, cudaEvent_t ev0, cudaEvent_t ev1) 
   a.H = h->H;
   a.nsweeps = nsweeps;
   a.lam = h->lam;
+  a.omega = h->omega;
   a.Sp = h->Sp;
   for (int i = 0; i < HQ_MAXN + 2; i++) {
     a.off[i] = h->off[i];

@@ -32,7 +32,7 @@ class hq_opts(ctypes.Structure):
                 ("precision", ctypes.c_int), ("check_every", ctypes.c_int),
                 ("warm_start", ctypes.c_int), ("warm_mem", ctypes.c_int),
                 ("warm_p", ctypes.c_void_p), ("fp32_stall", ctypes.c_double),
-                ("reserved", ctypes.c_int * 6)]
+                ("omega", ctypes.c_double), ("reserved", ctypes.c_int * 4)]
 
 
 class hq_stats(ctypes.Structure):
@@ -41,10 +41,10 @@ class hq_stats(ctypes.Structure):
                 ("final_step", ctypes.c_double), ("final_residual", ctypes.c_double),
                 ("ms_total", ctypes.c_double), ("ms_table", ctypes.c_double),
                 ("state_updates", ctypes.c_double), ("warm_used", ctypes.c_int),
-                ("reserved", ctypes.c_int * 5)]
+                ("pad0", ctypes.c_int), ("omega", ctypes.c_double), ("reserved", ctypes.c_int * 2)]
 
     def as_dict(self) -> dict:
-        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+        return {k: getattr(self, k) for k, _ in self._fields_ if k not in ("reserved", "pad0")}
 
 
 class HQError(RuntimeError):
@@ -402,7 +402,8 @@ class Solver:
         hq_load(self.h, lam_j, nu, pref)
 
     def solve(self, tol=1e-10, tol_kind=HQ_TOL_RESIDUAL, precision="fp32+df64", max_sweeps=100000,
-              check_every=8, warm_p=None, fp32_stall=0.0, warm_mlp=False) -> tuple[int, dict]:
+              check_every=8, warm_p=None, fp32_stall=0.0, warm_mlp=False,
+              omega=1.0) -> tuple[int, dict]:
         o = hq_default_opts()
         o.tol = tol
         o.tol_kind = tol_kind
@@ -410,6 +411,7 @@ class Solver:
         o.max_sweeps = max_sweeps
         o.check_every = check_every
         o.fp32_stall = fp32_stall
+        o.omega = omega
         keep = None
         if warm_p is not None:
             p, m = _ptr(np.ascontiguousarray(warm_p, dtype=np.float64)

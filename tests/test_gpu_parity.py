@@ -280,3 +280,34 @@ def test_large_n24_sampled(gpu_lib):
     assert np.max(np.abs(inst.lam_j @ R - inst.nu * rho)) <= bound
     assert np.allclose(R.sum(axis=1), 1.0, rtol=0, atol=1e-10)
     assert summ["residual"] < 1e-10
+
+
+# ---- over-relaxation (not in the paper): same fixed point, fewer sweeps ------------------
+
+@pytest.mark.parametrize("prec,omega", [("fp64", -1.0), ("fp32+df64", -1.0), ("df64", 1.3)])
+@pytest.mark.parametrize("N,J,mode,C,seed", CASES)
+def test_relaxed_solve_matches_oracle(gpu_lib, N, J, mode, C, seed, prec, omega):
+    inst = I.geometric_instance(N, J, seed, 0.7, nu_lo=0.5, nu_hi=1.5, mode=mode, C=C)
+    g = _solve_gpu(inst, tol=1e-13, tol_kind=hq.HQ_TOL_RESIDUAL, precision=prec, omega=omega)
+    assert g["rc"] == hq.HQ_OK, g["stats"]
+    assert g["stats"]["omega"] >= 1.0
+    r = oracle.solve(inst, eps=1e-15)
+    assert np.max(np.abs(g["P"] - r["P"])) < 1e-10
+    assert np.max(np.abs(g["rho"] - r["rho"])) < 1e-10
+    assert np.max(np.abs(g["R"] - r["R"])) < 1e-10
+
+
+def test_relaxation_saves_sweeps_and_rejects_bad_omega(gpu_lib):
+    inst = I.mixed_n20(2001, 0.6)
+    s = hq.Solver.for_instance(inst)
+    rc1, plain = s.solve(tol=1e-10, precision="fp64")
+    P1 = s.stationary()
+    rc2, relaxed = s.solve(tol=1e-10, precision="fp64", omega=-1.0)
+    assert rc1 == rc2 == hq.HQ_OK
+    assert relaxed["sweeps_hi"] < plain["sweeps_hi"] and relaxed["omega"] > 1.0
+    assert np.max(np.abs(s.stationary() - P1)) < 1e-9
+    for bad in (0.5, 2.0, 3.0):
+        with pytest.raises(hq.HQError) as e:
+            s.solve(tol=1e-10, precision="fp64", omega=bad)
+        assert e.value.code == hq.HQ_EINVAL
+    s.close()
