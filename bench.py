@@ -50,6 +50,8 @@ WORKLOADS = {
 SWEEP_DRAM_PER_ALG_BYTE = 297.768e6 / 251658120
 TRAFFIC_SOURCE = ("ncu --set full of one FP32 sweep at N=22 (profiles/k_persist_fp32_n22_set_full.md): "
                   "297.8 MB DRAM for 251.7 MB algorithmic, scaled by algorithmic bytes")
+METRIC = ("state-updates/s (solve to 1e-10 relative balance residual; N=24 time-to-tol, "
+          "FP32+refinement vs plain FP64, reported beside it)")
 BASE_SEED = {"n24": 3001, "n23": 3001, "n22": 3001, "n20": 2001, "n10": 1001}
 
 
@@ -97,6 +99,18 @@ def run_profile(args):
     s.close()
     print(json.dumps({"profile": inst.name, "sweeps": st["sweeps_hi"], "rc": rc}))
     return 0
+
+
+def reduce_over_ranks(ms: float, sweeps: float, device) -> tuple[float, float]:
+    """Replicas: the job's time is the slowest rank's, its work the sum of the ranks'."""
+    import torch
+    import torch.distributed as dist
+
+    tm = torch.tensor([ms], dtype=torch.float64, device=device)
+    ts = torch.tensor([sweeps], dtype=torch.float64, device=device)
+    dist.all_reduce(tm, op=dist.ReduceOp.MAX)
+    dist.all_reduce(ts, op=dist.ReduceOp.SUM)
+    return float(tm[0]), float(ts[0])
 
 
 def dist_info():
@@ -215,7 +229,7 @@ def run_reference(args):
     states = math.comb(N, n)
     total = sum(times)
     value = states * len(times) / total
-    line = {"metric": "state-updates/s (Algorithm 1, CPU oracle)", "value": value,
+    line = {"metric": METRIC, "value": value,
             "unit": "state-updates/s", "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000 * total / len(times), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -306,13 +320,7 @@ def run_ours(args):
         barrier()
         ms = ev0.elapsed_time(ev1)
         if ws > 1:
-            import torch.distributed as dist
-
-            t = torch.tensor([ms, float(sweeps_total)], dtype=torch.float64, device=dev)
-            tm = t.clone()
-            dist.all_reduce(tm[:1], op=dist.ReduceOp.MAX)
-            dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
-            ms, sweeps_all = float(tm[0]), float(t[1])
+            ms, sweeps_all = reduce_over_ranks(ms, float(sweeps_total), dev)
         else:
             sweeps_all = float(sweeps_total)
         value = (S - 2) * sweeps_all / (ms / 1000.0)
@@ -401,8 +409,7 @@ def run_ours(args):
         cpu = cpu_oracle_sample(inst)
     st0 = stats[-1]
     line = {
-        "metric": "state-updates/s (solve to 1e-10 relative balance residual; N=24 time-to-tol, "
-                  "FP32+refinement vs plain FP64, reported beside it)",
+        "metric": METRIC,
         "value": value, "unit": "state-updates/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+df64 (fp64 scalars)",
@@ -446,12 +453,13 @@ def run_batch(args):
         v, ms = hq.hq_batch_tune(b, pc, 4)
         tuned[name] = {"variant": v, "ms_per_sweep": [round(float(x), 4) for x in ms]}
 
-    def opts():
+    def opts(omega=args.omega):
         o = hq.hq_default_opts()
         o.tol = args.tol
         o.tol_kind = hq.HQ_TOL_STEP
         o.precision = prec
         o.check_every = 8
+        o.omega = omega
         return o
 
     for _ in range(max(1, args.warmup)):
@@ -489,7 +497,8 @@ def run_batch(args):
         "warmup": args.warmup, "ms_per_step": 1000 * t_batch, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
         "config": {"workload": f"batch{K}_n12_18_j200", "instances": K, "largest_N": int(info[1]),
-                   "states": int(info[2]), "tol_step": args.tol, "precision": args.precision},
+                   "states": int(info[2]), "tol_step": args.tol, "precision": args.precision,
+                   "omega": "automatic" if args.omega < 0 else args.omega},
         "state_updates_per_s": upd / t_batch, "converged": conv,
         "graph": {1: "captured graph replayed", -1: "capture refused: direct launches",
                   0: "not run"}[int(info[4])],

@@ -235,7 +235,8 @@ int hq_dispatch_table_static(int N, int J, const double* lambda_j, const int32_t
  *   Untuned precisions use variant 0.  Overwrites the solvers' iterates.
  * hq_batch_solve: solves every instance cold to opts->tol on Algorithm 1's step
  *   (opts->tol_kind must be HQ_TOL_STEP; warm starts are not supported); precision,
- *   check_every, max_sweeps and fp32_stall as for hq_solve (a mixed precision leaves
+ *   check_every, max_sweeps, fp32_stall and omega (per instance) as for hq_solve (a
+ *   mixed precision leaves
  *   FP32 for every instance at once, when all have stalled).  Each check replays one
  *   captured CUDA graph: [reset step buffers, one cooperative launch of check_every
  *   sweeps, copy the steps to the host].  Then each solver is finalised as hq_solve does

@@ -72,6 +72,7 @@ struct BatchArgs {
   int cfirst[HQ_MAXN + 2];  // fold entries of phase n
   const BCfg* cfg;
   const int* active;        // K flags
+  const double* omega;      // K over-relaxations of the finalised layers (1: none)
   const uint4* items;       // the instances' items, phase by phase
   const int* icfg;          // instance of each item
   const uint4* fchunks;     // {instance, layer, first rank, count} of the finalise chunks
@@ -168,13 +169,16 @@ __global__ void __launch_bounds__(kThreads, 2) k_batch(BatchArgs a) {
         const BCfg& C = a.cfg[c];
         const int lf = (int)f.y;
         const T c1 = V::from_d(__ldcg(&C.sc->c1[lf])), c2 = V::from_d(__ldcg(&C.sc->c2[lf]));
+        const double omd = a.omega[c];
+        const T om = V::from_d(omd);
         const P2* abf = (const P2*)((par ^ 1) ? C.ab1 : C.ab0);
         T* pl = (T*)C.p[PS] + C.off[lf];
         float md = 0.f;
         for (uint32_t q = f.z + lane; q < f.z + f.w; q += 32) {
           const P2 ab = ld_l2(abf + q);
           const T old = ld_l2(pl + q);
-          const T v = V::add(V::mul(c1, PR::A(ab)), V::mul(c2, PR::B(ab)));
+          T v = V::add(V::mul(c1, PR::A(ab)), V::mul(c2, PR::B(ab)));
+          if (omd != 1.0) v = V::add(old, V::mul(om, V::sub(v, old)));
           md = fmaxf(md, V::absdiff(v, old));
           pl[q] = v;
         }
@@ -295,6 +299,7 @@ struct hq_batch {
   std::vector<BCfg> hcfg;
   BCfg* cfg = nullptr;
   int* active = nullptr;
+  double* omega = nullptr;
   uint4* items = nullptr;
   int* icfg = nullptr;
   uint4* fchunks = nullptr;
@@ -413,7 +418,8 @@ int run_check(hq_batch* b, int prec, int variant, int nsweeps) {
 }
 
 void free_batch(hq_batch* b) {
-  void* ptrs[] = {b->cfg, b->active, b->items, b->icfg, b->fchunks, b->folds, b->ipart, b->step_bits, b->bar};
+  void* ptrs[] = {b->cfg, b->active, b->omega, b->items, b->icfg, b->fchunks, b->folds, b->ipart,
+                  b->step_bits, b->bar};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (b->hstep) cudaFreeHost(b->hstep);
@@ -557,6 +563,7 @@ extern "C" int hq_batch_create(hq_solver* const* solvers, int count, void* strea
   std::vector<int> act(count, 1);
   int rc = dupload(&b->cfg, b->hcfg);
   if (rc == HQ_OK) rc = dupload(&b->active, act);
+  if (rc == HQ_OK) rc = dupload(&b->omega, std::vector<double>(count, 1.0));
   if (rc == HQ_OK) rc = dupload(&b->items, items);
   if (rc == HQ_OK) rc = dupload(&b->icfg, icfg);
   if (rc == HQ_OK) rc = dupload(&b->fchunks, fchunks);
@@ -585,6 +592,7 @@ extern "C" int hq_batch_create(hq_solver* const* solvers, int count, void* strea
   }
   a.cfg = b->cfg;
   a.active = b->active;
+  a.omega = b->omega;
   a.items = b->items;
   a.icfg = b->icfg;
   a.fchunks = b->fchunks;
@@ -628,7 +636,10 @@ extern "C" int hq_batch_tune(hq_batch* b, int precision, int sweeps, int* varian
   int rc = on_batch_stream(b, [&](hq_solver* h) { return hq_init_iterate(h, precision, nullptr, HQ_HOST); });
   if (rc != HQ_OK) return rc;
   std::vector<int> act(b->K, 1);
+  std::vector<double> om1(b->K, 1.0);
   HQ_CUDA(cudaMemcpyAsync(b->active, act.data(), sizeof(int) * b->K, cudaMemcpyHostToDevice, b->stream));
+  HQ_CUDA(cudaMemcpyAsync(b->omega, om1.data(), sizeof(double) * b->K, cudaMemcpyHostToDevice, b->stream));
+  HQ_CUDA(cudaStreamSynchronize(b->stream));
   cudaEvent_t e0, e1;
   HQ_CUDA(cudaEventCreate(&e0));
   HQ_CUDA(cudaEventCreate(&e1));
@@ -676,6 +687,11 @@ extern "C" int hq_batch_solve(hq_batch* b, const hq_opts* opts_in, hq_stats* sta
   if (o.warm_start != HQ_WARM_NONE) { hq_set_error("batched solves start cold"); return HQ_EINVAL; }
   if (o.check_every < 1) o.check_every = 1;
   if (o.precision < HQ_PREC_FP64 || o.precision > HQ_PREC_FP32_FP64) { hq_set_error("bad precision"); return HQ_EINVAL; }
+  if (!(o.omega < 2.0) || (o.omega >= 0.0 && o.omega < 1.0 && o.omega != 0.0)) {
+    hq_set_error("omega must be 0, in [1, 2), or negative (automatic)");
+    return HQ_EINVAL;
+  }
+  const bool auto_omega = o.omega < 0.0;
   const double stall = o.fp32_stall > 0.0 ? o.fp32_stall : 0.9;
   auto t0 = std::chrono::steady_clock::now();
   int phases[2];
@@ -694,8 +710,10 @@ extern "C" int hq_batch_solve(hq_batch* b, const hq_opts* opts_in, hq_stats* sta
   });
   if (rc != HQ_OK) return rc;
   std::vector<int> act(K, 1), conv(K, 0), sw32(K, 0), swhi(K, 0), stalled(K, 0), flat(K, 0);
-  std::vector<double> step(K, INFINITY), prev(K, 0.0);
+  std::vector<double> step(K, INFINITY), prev(K, 0.0), om(K, o.omega >= 1.0 ? o.omega : 1.0);
+  std::vector<int> checks(K, 0);
   HQ_CUDA(cudaMemcpyAsync(b->active, act.data(), sizeof(int) * K, cudaMemcpyHostToDevice, b->stream));
+  HQ_CUDA(cudaMemcpyAsync(b->omega, om.data(), sizeof(double) * K, cudaMemcpyHostToDevice, b->stream));
   HQ_CUDA(cudaMemsetAsync(b->bar + 2, 0, sizeof(unsigned), b->stream));
   int ph = 0, total = 0, status = HQ_OK;
   while (total < o.max_sweeps) {
@@ -722,6 +740,17 @@ extern "C" int hq_batch_solve(hq_batch* b, const hq_opts* opts_in, hq_stats* sta
       step[c] = f;
       if (!isfinite(step[c]) || (flags & 1u)) status = HQ_EDIVERGED;
       const double ratio = prev[c] > 0.0 ? step[c] / prev[c] : 0.0;
+      if (auto_omega) {
+        // as hq_solve: Young's omega for the contraction over the third check, 90 % of its
+        // extrapolation, at most 1.5; halfway back whenever the steps stop shrinking
+        checks[c]++;
+        if (om[c] == 1.0 && checks[c] == 3 && ratio > 0.0 && ratio < 1.0) {
+          const double r = pow(ratio, 1.0 / nrun);
+          om[c] = fmin(1.0 + 0.9 * (2.0 / (1.0 + sqrt(1.0 - r)) - 1.0), 1.5);
+        } else if (om[c] > 1.0 && ratio >= 1.0) {
+          om[c] = 1.0 + 0.5 * (om[c] - 1.0);
+        }
+      }
       if (ph == nph - 1) {
         if (step[c] <= o.tol) {
           conv[c] = 1;
@@ -756,6 +785,7 @@ extern "C" int hq_batch_solve(hq_batch* b, const hq_opts* opts_in, hq_stats* sta
       }
     }
     HQ_CUDA(cudaMemcpyAsync(b->active, act.data(), sizeof(int) * K, cudaMemcpyHostToDevice, b->stream));
+    HQ_CUDA(cudaMemcpyAsync(b->omega, om.data(), sizeof(double) * K, cudaMemcpyHostToDevice, b->stream));
   }
   HQ_CUDA(cudaStreamSynchronize(b->stream));
   for (hq_solver* h : b->s) h->cur_prec = phases[ph];
@@ -781,6 +811,7 @@ extern "C" int hq_batch_solve(hq_batch* b, const hq_opts* opts_in, hq_stats* sta
       st.final_residual = res[c];
       st.ms_table = b->s[c]->ms_table;
       st.state_updates = (double)(b->s[c]->S - 2) * (double)(sw32[c] + swhi[c]);
+      st.omega = om[c];
     }
   }
   if (ms_total) *ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();

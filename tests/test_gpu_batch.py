@@ -26,8 +26,9 @@ def _instances(cases=MIXED, load=0.7):
             for N, J, mode, C, seed in cases]
 
 
-def _opts(prec, tol, max_sweeps=100000, check_every=8):
+def _opts(prec, tol, max_sweeps=100000, check_every=8, omega=1.0):
     o = hq.hq_default_opts()
+    o.omega = omega
     o.tol = tol
     o.tol_kind = hq.HQ_TOL_STEP
     o.precision = hq.PRECISION[prec]
@@ -51,10 +52,12 @@ def _batch_solve(insts, prec, tol, **kw):
     return rc, stats, out, info
 
 
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-14), ("df64", 1e-13), ("fp32+df64", 1e-13)])
-def test_batch_matches_oracle(gpu_lib, prec, tol):
+@pytest.mark.parametrize("prec,tol,omega", [("fp64", 1e-14, 1.0), ("df64", 1e-13, 1.0),
+                                            ("fp32+df64", 1e-13, 1.0), ("fp64", 1e-14, -1.0),
+                                            ("fp32+df64", 1e-13, -1.0)])
+def test_batch_matches_oracle(gpu_lib, prec, tol, omega):
     insts = _instances()
-    rc, stats, out, info = _batch_solve(insts, prec, tol)
+    rc, stats, out, info = _batch_solve(insts, prec, tol, omega=omega)
     assert rc == hq.HQ_OK, stats
     assert info[0] == len(insts) and info[1] == 13
     assert info[4] in (1, -1)  # checks replayed a captured graph, or launched directly
