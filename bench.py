@@ -47,9 +47,9 @@ WORKLOADS = {
 # bench's launch is too large to capture, so its traffic is this ratio times its
 # algorithmic bytes (traffic grows in proportion to the states swept).  None once the
 # kernel has changed since the capture.
-SWEEP_DRAM_PER_ALG_BYTE = 297.768e6 / 251658120
+SWEEP_DRAM_PER_ALG_BYTE = 298.148e6 / 251658120
 TRAFFIC_SOURCE = ("ncu --set full of one FP32 sweep at N=22 (profiles/k_persist_fp32_n22_set_full.md): "
-                  "297.8 MB DRAM for 251.7 MB algorithmic, scaled by algorithmic bytes")
+                  "298.1 MB DRAM for 251.7 MB algorithmic, scaled by algorithmic bytes")
 METRIC = ("state-updates/s (solve to 1e-10 relative balance residual; N=24 time-to-tol, "
           "FP32+refinement vs plain FP64, reported beside it)")
 BASE_SEED = {"n24": 3001, "n23": 3001, "n22": 3001, "n20": 2001, "n10": 1001}

@@ -49,7 +49,8 @@ namespace {
 
 using namespace hqdev;
 
-constexpr int kThreads = 512;             // 16 warps, two CTAs per SM at 64 registers
+constexpr int kThreads = 1024;            // 32 warps, one CTA per SM at 64 registers:
+                                          // half the grid arrivals and partials of 2 x 512
 constexpr int kWarps = kThreads / 32;
 constexpr int kPW = 6;                    // partial words per CTA per phase
 constexpr unsigned kSpinLimit = 1u << 24;
@@ -84,7 +85,7 @@ struct PersistArgs {
 };
 
 template <class V>
-__global__ void __launch_bounds__(kThreads, 2) k_persist(PersistArgs a) {
+__global__ void __launch_bounds__(kThreads, 1) k_persist(PersistArgs a) {
   typedef typename V::T T;
   typedef Pair<V> PR;
   typedef typename PR::P P2;
