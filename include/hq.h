@@ -228,10 +228,11 @@ int hq_dispatch_table_static(int N, int J, const double* lambda_j, const int32_t
  *   combined work lists (host memory for the build, device memory for the lists).
  *   Errors: HQ_EINVAL (NULL, count < 1, N < 2, another device), HQ_ESTATE (a solver not
  *   loaded), HQ_ENOMEM.
- * hq_batch_tune: the autotuner.  Times each kernel variant (chunk widths of the gathers,
- *   CTAs per SM) for `sweeps` sweeps of `precision` (HQ_PREC_FP64, _DF64 or _FP32) from
- *   a cold start and keeps the fastest for later solves; variant_out (may be NULL)
- *   receives it, ms_out (may be NULL, 4 floats) the ms per sweep of each variant.
+ * hq_batch_tune: the autotuner.  Times each kernel variant (threads per CTA x CTAs per
+ *   SM: 0 = 512 x 2, 1 = 1024 x 1, 2 = 512 x 1, 3 = 256 x up to 4) for `sweeps` sweeps of
+ *   `precision` (HQ_PREC_FP64, _DF64 or _FP32) from a cold start and keeps the fastest
+ *   for later solves; variant_out (may be NULL) receives it, ms_out (may be NULL, 4
+ *   floats) the ms per sweep of each variant.
  *   Untuned precisions use variant 0.  Overwrites the solvers' iterates.
  * hq_batch_solve: solves every instance cold to opts->tol on Algorithm 1's step
  *   (opts->tol_kind must be HQ_TOL_STEP; warm starts are not supported); precision,

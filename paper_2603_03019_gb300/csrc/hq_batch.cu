@@ -19,7 +19,7 @@
 // back] until every instance's step is below the tolerance; that sequence is captured
 // once as a CUDA graph and replayed.  Mixed precision runs FP32 sweeps until the FP32
 // steps stop shrinking, then converts every instance to DF64 (or FP64).  The kernel
-// variant (chunk widths and CTAs per SM) is chosen by hq_batch_tune from timed sweeps.
+// variant (CTA size and CTAs per SM) is chosen by hq_batch_tune from timed sweeps.
 //
 // Every wait is bounded (the two grid barriers); a timeout sets a flag and the host
 // reports HQ_ETIMEOUT.
@@ -35,10 +35,12 @@ namespace {
 
 using namespace hqdev;
 
-constexpr int kThreads = 512;
-constexpr int kWarps = kThreads / 32;
 constexpr unsigned kSpinLimit = 1u << 24;
-constexpr int kVariants = 4;  // {wide, narrow chunks} x {2, 1} CTAs per SM
+// the kernel variants the tuner chooses among: threads per CTA and CTAs per SM (at most;
+// fewer where shared memory does not allow them), all at 64 registers per thread
+constexpr int kVariants = 4;
+constexpr int kVarThreads[kVariants] = {512, 1024, 512, 256};
+constexpr int kVarCtas[kVariants] = {2, 1, 1, 4};
 
 // per-instance view for the device (one array entry per instance)
 struct BCfg {
@@ -82,16 +84,19 @@ struct BatchArgs {
   unsigned* bar;            // [0] arrivals, [1] generation, [2] flags
 };
 
-template <class V, int CB, int CI>
-__global__ void __launch_bounds__(kThreads, 2) k_batch(BatchArgs a) {
+template <class V, int kThreads>
+__global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_batch(BatchArgs a) {
   typedef typename V::T T;
   typedef Pair<V> PR;
   typedef typename PR::P P2;
   constexpr int PS = PSlot<V>::v;
+  constexpr int kWarps = kThreads / 32;
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ uint32_t s_RL[1 << HQ_LO_BITS];
   __shared__ int s_bin[HQ_LO_BITS + 1][HQ_LO_BITS + 2];  // s_bin[L][i] = C(L, i - 1)
   __shared__ double s_red[4][kWarps];
+  __shared__ uint32_t s_hl[kWarps][32];  // per warp: the item's high-part neighbour bases
+  __shared__ T s_hnu[kWarps][32];        // and its idle high-part units' rates
   __shared__ unsigned s_gen0;
 
   const unsigned G = gridDim.x;
@@ -213,8 +218,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_batch(BatchArgs a) {
         lv.lamT = V::from_d(C.lam);
         lv.one = V::from_d(1.0);
         T sA = V::zero(), sB = V::zero(), sa = V::zero(), sb = V::zero();
-        gather_item<V, CB, CI>(lv, __ldg(a.items + it), s_RL, s_bin[C.L], slot_d, slot_u, lane, sA, sB, sa,
-                               sb);
+        gather_item<V, false>(lv, __ldg(a.items + it), s_RL, s_bin[C.L], slot_d, slot_u, s_hl[wid],
+                              s_hnu[wid], lane, sA, sB, sa, sb);
         __syncwarp();
         sA = warp_sum<V>(sA);
         sB = warp_sum<V>(sB);
@@ -275,17 +280,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_batch(BatchArgs a) {
   }
 }
 
-// The kernel variants the tuner chooses among: chunk widths per precision (busy, idle
-// loads in flight per chunk) and CTAs per SM.
-template <class V> struct Wide { static constexpr int b = 2, i = 2; };
-template <> struct Wide<PolF32> { static constexpr int b = 4, i = 4; };
-template <class V> struct Narrow { static constexpr int b = 1, i = 2; };
-template <> struct Narrow<PolF32> { static constexpr int b = 2, i = 4; };
-
 template <class V>
 const void* kernel_of(int variant) {
-  if ((variant & 1) == 0) return (const void*)k_batch<V, Wide<V>::b, Wide<V>::i>;
-  return (const void*)k_batch<V, Narrow<V>::b, Narrow<V>::i>;
+  const int t = kVarThreads[variant];
+  if (t == 1024) return (const void*)k_batch<V, 1024>;
+  if (t == 256) return (const void*)k_batch<V, 256>;
+  return (const void*)k_batch<V, 512>;
 }
 
 }  // namespace
@@ -323,12 +323,12 @@ namespace {
 int slot_of(int prec) { return prec == HQ_PREC_FP64 ? 0 : (prec == HQ_PREC_DF64 ? 1 : 2); }
 
 template <class V>
-size_t smem_of() { return (size_t)kWarps * Slot<V>::kBytes; }
+size_t smem_of(int variant) { return (size_t)(kVarThreads[variant] / 32) * Slot<V>::kBytes; }
 
-size_t smem_for(int prec) {
-  if (prec == HQ_PREC_FP64) return smem_of<PolF64>();
-  if (prec == HQ_PREC_DF64) return smem_of<PolDF>();
-  return smem_of<PolF32>();
+size_t smem_for(int prec, int variant) {
+  if (prec == HQ_PREC_FP64) return smem_of<PolF64>(variant);
+  if (prec == HQ_PREC_DF64) return smem_of<PolDF>(variant);
+  return smem_of<PolF32>(variant);
 }
 
 const void* kernel_for(int prec, int variant) {
@@ -339,15 +339,15 @@ const void* kernel_for(int prec, int variant) {
 
 int grid_for(hq_batch* b, int prec, int variant, int* G) {
   const void* k = kernel_for(prec, variant);
-  const size_t sm = smem_for(prec);
+  const size_t sm = smem_for(prec, variant);
   HQ_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
   int occ = 0;
-  HQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, kThreads, sm));
+  HQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, kVarThreads[variant], sm));
   if (occ < 1) {
     hq_set_error("batched sweep kernel does not fit on an SM");
     return HQ_ECUDA;
   }
-  const int want = (variant & 2) ? 1 : 2;
+  const int want = kVarCtas[variant];
   *G = b->nsm * (occ < want ? occ : want);
   return HQ_OK;
 }
@@ -366,8 +366,8 @@ int record_check(hq_batch* b, int prec, int variant, int nsweeps) {
   cudaLaunchConfig_t lc;
   memset(&lc, 0, sizeof(lc));
   lc.gridDim = dim3(G);
-  lc.blockDim = dim3(kThreads);
-  lc.dynamicSmemBytes = smem_for(prec);
+  lc.blockDim = dim3(kVarThreads[variant]);
+  lc.dynamicSmemBytes = smem_for(prec, variant);
   lc.stream = b->stream;
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeCooperative;

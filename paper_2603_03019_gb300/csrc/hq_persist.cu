@@ -33,9 +33,10 @@
 // gather reads shared memory; the positions there come precomputed per state (lidx).
 // Neighbours across a high-part unit, and the table rows, are read with coalesced loads
 // straight from global memory: one lane per state, consecutive states at consecutive
-// addresses.  Loads are issued in chunks before their values are used, so many are
-// in flight per thread.  There is no producer, no stage ring and no wait other than the
-// grid barrier.
+// addresses.  The gather has no per-neighbour branch: the low-part steps are unrolled
+// over the lidx bytes, the high-part ones run over a per-warp list of the item's
+// neighbour blocks, and the low-part table entries are loaded before the staging wait.
+// There is no producer, no stage ring and no wait other than the grid barrier.
 //
 // The grid barrier's wait is bounded: a barrier that does not complete within its
 // iteration limit sets an error bit in DevScalars::flags and the kernel runs to its end
@@ -54,10 +55,6 @@ constexpr int kThreads = 1024;            // 32 warps, one CTA per SM at 64 regi
 constexpr int kWarps = kThreads / 32;
 constexpr int kPW = 6;                    // partial words per CTA per phase
 constexpr unsigned kSpinLimit = 1u << 24;
-
-// loads in flight per thread per chunk (busy, idle neighbours), within 64 registers
-template <class V> struct Chunk { static constexpr int b = 2, i = 2; };
-template <> struct Chunk<PolF32> { static constexpr int b = 4, i = 4; };
 
 struct PersistArgs {
   int N, L, H, nsweeps;
@@ -84,12 +81,11 @@ struct PersistArgs {
   DevScalars* sc;
 };
 
-template <class V>
+template <class V, bool kFullL>
 __global__ void __launch_bounds__(kThreads, 1) k_persist(PersistArgs a) {
   typedef typename V::T T;
   typedef Pair<V> PR;
   typedef typename PR::P P2;
-  constexpr int CB = Chunk<V>::b, CI = Chunk<V>::i;
   // per-warp slots: staged (A, B) block of layer n-1, then staged p block of layer n+1
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ uint32_t s_RL[1 << HQ_LO_BITS];
@@ -97,6 +93,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_persist(PersistArgs a) {
   __shared__ double s_lam[HQ_MAXN + 1], s_mu[HQ_MAXN + 1];
   __shared__ T s_nu[HQ_MAXN];
   __shared__ double s_red[kPW][kWarps];
+  __shared__ uint32_t s_hl[kWarps][32];  // per warp: the item's high-part neighbour bases
+  __shared__ T s_hnu[kWarps][32];        // and its idle high-part units' rates
   __shared__ T s_lamT, s_one;
   __shared__ T s_c1, s_c2;
   __shared__ double s_step[2];
@@ -309,8 +307,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_persist(PersistArgs a) {
       for (; it < it_end; it += nwarps) {
         const uint4 d = dnext;
         if (it + nwarps < it_end) dnext = __ldg(a.items + it + nwarps);  // next item, ahead
-        gather_item<V, CB, CI>(lv, d, s_RL, s_binL, slot_d, slot_u, lane, sA, sB, sa, sb);
-        __syncwarp();  // the slot is restaged by the next item
+        gather_item<V, kFullL>(lv, d, s_RL, s_binL, slot_d, slot_u, s_hl[wid], s_hnu[wid], lane, sA, sB,
+                               sa, sb);
+        __syncwarp();  // the slot and the lists are rewritten by the next item
       }
       sync_phase(sA, sB, sa, sb, md, n, n >= 2 ? k : k - 1);
     }
@@ -334,7 +333,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_persist(PersistArgs a) {
   }
 }
 
-int g_occ[3] = {0, 0, 0};
+int g_occ[3][2] = {{0, 0}, {0, 0}, {0, 0}};
 int g_nsm = 0;
 
 template <class V>
@@ -343,17 +342,19 @@ int launch_persist(hq_solver* h, int nsweeps, cudaEvent_t ev0, cudaEvent_t ev1) 
   typedef typename Pair<V>::P P2;
   const int slot = V::kind == HQ_PREC_FP64 ? 0 : (V::kind == HQ_PREC_DF64 ? 1 : 2);
   const size_t smem = (size_t)kWarps * Slot<V>::kBytes;
+  const bool full = h->L == HQ_LO_BITS;
+  const void* kfn = full ? (const void*)k_persist<V, true> : (const void*)k_persist<V, false>;
   if (!g_nsm) HQ_CUDA(cudaDeviceGetAttribute(&g_nsm, cudaDevAttrMultiProcessorCount, h->dev));
-  if (!g_occ[slot]) {
-    HQ_CUDA(cudaFuncSetAttribute(k_persist<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  if (!g_occ[slot][full]) {
+    HQ_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   }
   int occ = 0;
-  HQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_persist<V>, kThreads, smem));
+  HQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kfn, kThreads, smem));
   if (occ < 1) {
     hq_set_error("persistent sweep kernel does not fit on an SM");
     return HQ_ECUDA;
   }
-  g_occ[slot] = occ;
+  g_occ[slot][full] = occ;
   const int G = g_nsm * occ;
   if ((int64_t)G * (nsweeps * (int64_t)(h->N - 1) + 1) >= ((int64_t)1 << 31)) {
     hq_set_error("too many barrier arrivals for one launch");
@@ -399,8 +400,7 @@ int launch_persist(hq_solver* h, int nsweeps, cudaEvent_t ev0, cudaEvent_t ev1) 
   // a barrier left half-entered by an aborted launch must not leak into this one
   HQ_CUDA(cudaMemsetAsync(&h->sc->bar_count, 0, sizeof(unsigned), h->stream));
   if (ev0) HQ_CUDA(cudaEventRecord(ev0, h->stream));
-  HQ_CUDA(cudaLaunchCooperativeKernel((const void*)k_persist<V>, dim3(G), dim3(kThreads), args, smem,
-                                      h->stream));
+  HQ_CUDA(cudaLaunchCooperativeKernel(kfn, dim3(G), dim3(kThreads), args, smem, h->stream));
   HQ_LAUNCHED();
   if (ev1) HQ_CUDA(cudaEventRecord(ev1, h->stream));
   return HQ_OK;

@@ -115,24 +115,47 @@ template <class V> struct LayerView {
 // Gather one item of layer n (Eq. 12): A_m = r_m sum_s p_{n-1}(m - c_s) T[m][s] with
 // p_{n-1} = c1 A + c2 B of the previous layer, B_m = r_m sum_{u idle} p_{n+1}(m + u) nu_u,
 // written as (A, B) pairs; adds the item's sum mu_m A_m to sA, sum mu_m B_m to sB, sum A_m
-// to sa and sum B_m to sb (mu_m r_m = 1 - lambda r_m).  CB / CI: busy / idle neighbour
-// loads in flight per chunk.  The caller syncs the warp before the slot is restaged.
-template <class V, int CB, int CI>
+// to sa and sum B_m to sb (mu_m r_m = 1 - lambda r_m).
+//
+// The sums run in a fixed order whatever the layout of the loops: busy neighbours in
+// table-slot order (increasing unit), idle neighbours in increasing unit order.  Low part:
+// one step per lidx byte k < L (compile-time k, so the byte and the table row are
+// immediates; k < w busy from the staged block of layer n-1, else idle from the staged
+// block of layer n+1).  High part: counted loops over the warp's list `hl` of neighbour
+// block bases (the item's busy units first, then its idle units, each increasing) with
+// the idle units' rates in `hnu`; every lane reads the same entry.  kFullL: L equals
+// HQ_LO_BITS (every instance with N >= HQ_LO_BITS).  The caller syncs the warp before the
+// slot and the lists are rewritten by the next item.
+template <class V, bool kFullL>
 __device__ __forceinline__ void gather_item(const LayerView<V>& lv, const uint4 d, const uint32_t* s_RL,
                                             const int* s_binL, unsigned char* slot_d,
-                                            unsigned char* slot_u, int lane, typename V::T& sA,
-                                            typename V::T& sB, typename V::T& sa, typename V::T& sb) {
+                                            unsigned char* slot_u, uint32_t* hl, typename V::T* hnu,
+                                            int lane, typename V::T& sA, typename V::T& sB,
+                                            typename V::T& sa, typename V::T& sb) {
   typedef typename V::T T;
   typedef Pair<V> PR;
   typedef typename PR::P P2;
-  const int n = lv.n, N = lv.N, L = lv.L, H = lv.H;
-  const uint32_t lmask = (1u << L) - 1u, hmask = (1u << H) - 1u;
+  const int n = lv.n, L = kFullL ? HQ_LO_BITS : lv.L, H = lv.H;
+  const uint32_t lmask = (1u << L) - 1u;
   const uint32_t rank0 = d.x;
   const uint32_t hi = d.y & ((1u << HQ_ITEM_HI_BITS) - 1u);
   const int w = (int)((d.y >> HQ_ITEM_HI_BITS) & 0xfu);
   const int count = (int)((d.y >> 24) & 0x1fu) + 1;
-  // rank bases of the high-part neighbour blocks: lane j holds RH[hi ^ 2^j][w]
-  const uint32_t hbl = lane < H ? __ldg(lv.RH + (size_t)(hi ^ (1u << lane)) * (L + 1) + w) : 0u;
+  const bool pull = n > 1;  // layer 1 pulls from the empty state, whose p_0 = 1
+  const int nbh = n - w, nih = H - nbh;
+  // the high-part neighbour lists: lane j < H owns unit L + j, whose block base is
+  // RH[hi ^ 2^j][w] in layer n -/+ 1
+  if (lane < H) {
+    const uint32_t hb = __ldg(lv.RH + (size_t)(hi ^ (1u << lane)) * (L + 1) + w);
+    const uint32_t below = hi & ((1u << lane) - 1u);
+    if ((hi >> lane) & 1u) {
+      hl[__popc(below)] = hb;
+    } else {
+      const int k = lane - __popc(below);
+      hl[nbh + k] = hb;
+      hnu[k] = lv.nu[L + lane];
+    }
+  }
   // this lane's state (lanes past the item repeat its first state and discard it)
   const bool act = lane < count;
   const uint32_t kq = rank0 + (act ? (uint32_t)lane : 0u);
@@ -142,13 +165,18 @@ __device__ __forceinline__ void gather_item(const LayerView<V>& lv, const uint4 
                  iw2 = __ldg(lv.lidx + 2 * lv.Sp + gi);
   const T rv = __ldg(lv.rt + gi);
   const T* tcol = lv.Tt + lv.toff_n + kq;  // table slot s at tcol[s * lp]
+  const int64_t lp = lv.lp;
+  // table entries of the low-part busy neighbours, issued before the staging wait
+  T tlo[HQ_LO_BITS];
+#pragma unroll
+  for (int k = 0; k < HQ_LO_BITS; k++) tlo[k] = (k < w && pull) ? ld_stream(tcol + k * lp) : V::zero();
   // stage the low-part neighbour blocks in this warp's slot with 16-byte asynchronous
   // copies: a block's copy starts at the 16-byte boundary at or below its first
   // element (offset `dd` / `du` elements into the slot) and covers whole 16-byte units
   const P2* sdn;
   const T* sup;
   {
-    const int dc = (n > 1 && w > 0) ? s_binL[w] : 0;
+    const int dc = (pull && w > 0) ? s_binL[w] : 0;
     const int uc = w < L ? s_binL[w + 2] : 0;
     const unsigned char* gd = (const unsigned char*)(lv.ab_prev + d.z);
     const unsigned char* gu = (const unsigned char*)(lv.p_up + d.w);
@@ -163,76 +191,47 @@ __device__ __forceinline__ void gather_item(const LayerView<V>& lv, const uint4 
   }
   const uint32_t lo = x & lmask;
   const uint32_t rl = s_RL[lo];
-  __syncwarp();
+  __syncwarp();  // staged blocks and lists visible to the whole warp
   T UA = V::zero(), UB = V::zero(), D = V::zero();
-  // Busy neighbours in table-slot order (increasing unit): w low-part ones from the
-  // staged block, then the high part at rank RH[hi ^ 2^c][w] + RL[lo] of layer n-1.
-  // Idle neighbours, rate nu_u, in increasing unit order: L - w low-part ones from the
-  // staged block, then the high part at rank RH[hi ^ 2^c][w] + RL[lo] of layer n+1.
-  // One chunk takes CB busy and CI idle neighbours, so both chains advance together.
+  // low part: lidx byte k is the k-th busy unit's neighbour for k < w, else the
+  // (k - w)-th idle unit's (the idle units are the set bits of `z`, taken in order)
   {
-    const int nb = n > 1 ? n : 0, ni = N - n, nl = L - w;
-    uint32_t yb = hi, yl = ~lo & lmask, yh = ~hi & hmask;
-    for (int sb0 = 0, si0 = 0; sb0 < nb || si0 < ni; sb0 += CB, si0 += CI) {
-      P2 q[CB];
-      T tv[CB], v[CI];
-      const uint32_t yl0 = yl, yh0 = yh;
+    uint32_t z = ~lo & lmask;
 #pragma unroll
-      for (int j = 0; j < CB; j++) {
-        const int s = sb0 + j;
-        if (s < nb) {
-          tv[j] = ld_stream(tcol + s * lv.lp);
-          if (s < w) {
-            q[j] = sdn[lo_pos(iw0, iw1, iw2, s)];
-          } else {
-            const int c = __ffs(yb) - 1;
-            yb &= yb - 1;
-            q[j] = ld_l2(lv.ab_prev + __shfl_sync(0xffffffffu, hbl, c) + rl);
+    for (int k = 0; k < HQ_LO_BITS; k++) {
+      if (kFullL || k < L) {
+        const uint32_t wd = k < 4 ? iw0 : (k < 8 ? iw1 : iw2);
+        const int pos = (int)((wd >> (8 * (k & 3))) & 0xffu);
+        if (k < w) {
+          if (pull) {
+            const P2 q = sdn[pos];
+            V::fma_acc(UA, PR::A(q), tlo[k]);
+            V::fma_acc(UB, PR::B(q), tlo[k]);
           }
-        }
-      }
-#pragma unroll
-      for (int j = 0; j < CI; j++) {
-        const int s = si0 + j;
-        if (s < ni) {
-          if (s < nl) {
-            yl &= yl - 1;
-            v[j] = sup[lo_pos(iw0, iw1, iw2, w + s)];
-          } else {
-            const int c = __ffs(yh) - 1;
-            yh &= yh - 1;
-            v[j] = ld_l2(lv.p_up + __shfl_sync(0xffffffffu, hbl, c) + rl);
-          }
-        }
-      }
-#pragma unroll
-      for (int j = 0; j < CB; j++) {
-        if (sb0 + j < nb) {
-          V::fma_acc(UA, PR::A(q[j]), tv[j]);
-          V::fma_acc(UB, PR::B(q[j]), tv[j]);
-        }
-      }
-      uint32_t zl = yl0, zh = yh0;  // replay the unit order for the rates nu_u
-#pragma unroll
-      for (int j = 0; j < CI; j++) {
-        const int s = si0 + j;
-        if (s < ni) {
-          int u;
-          if (s < nl) {
-            u = __ffs(zl) - 1;
-            zl &= zl - 1;
-          } else {
-            u = L + __ffs(zh) - 1;
-            zh &= zh - 1;
-          }
-          V::fma_acc(D, v[j], lv.nu[u]);
+        } else {
+          const int u = __ffs(z) - 1;
+          z &= z - 1u;
+          V::fma_acc(D, sup[pos], lv.nu[u]);
         }
       }
     }
   }
+  // high part, busy: table slots w .. n-1
+  if (pull) {
+    const T* tp = tcol + w * lp;
+#pragma unroll 4
+    for (int k = 0; k < nbh; k++) {
+      const T t = ld_stream(tp + k * lp);
+      const P2 q = ld_l2(lv.ab_prev + hl[k] + rl);
+      V::fma_acc(UA, PR::A(q), t);
+      V::fma_acc(UB, PR::B(q), t);
+    }
+  }
+  // high part, idle
+#pragma unroll 4
+  for (int k = 0; k < nih; k++) V::fma_acc(D, ld_l2(lv.p_up + hl[nbh + k] + rl), hnu[k]);
   // up-inflow: layer 0 is the empty state with p_0 = 1
-  const T U = n == 1 ? ld_stream(tcol)
-                     : V::add(V::mul(lv.c1, V::norm(UA)), V::mul(lv.c2, V::norm(UB)));
+  const T U = pull ? V::add(V::mul(lv.c1, V::norm(UA)), V::mul(lv.c2, V::norm(UB))) : ld_stream(tcol);
   D = V::norm(D);
   const T qm = V::sub(lv.one, V::mul(lv.lamT, rv));  // mu_m r_m = 1 - lambda r_m
   const T A = V::mul(U, rv), B = V::mul(D, rv);
