@@ -3,12 +3,13 @@
 Workload (default): N=24 units, J=1000 clustered demand nodes, infinite queue,
 nu log-uniform on [1,3], load 0.8 -- 2^24 = 16.8M states.  One step = load the
 instance from device memory (validation + upward-rate table build), solve to a
-relative global-balance residual of 1e-10 (FP32 sweeps, then DF64 sweeps; FP64
-scalars and residual), and write P, rho, R, W to device memory.
+relative global-balance residual of 1e-10 (FP32 sweeps, then iterative refinement:
+FP32 sweeps of the correction against an FP64 base; FP64 base pass, layer scalars and
+residual), and write P, rho, R, W to device memory.
 
 Metric: state-updates/s = (2^N - 2) x sweeps / time, whole job.  Reported beside it:
 time-to-1e-10-residual of the plain FP64 iteration and of the other precision
-paths on the same instance and GPU, the DF64 sweep's HBM roofline, and the CPU
+paths on the same instance and GPU, the FP32 sweep's HBM roofline, and the CPU
 oracle timed on a bounded sample of the same workload.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
@@ -47,9 +48,13 @@ WORKLOADS = {
 # bench's launch is too large to capture, so its traffic is this ratio times its
 # algorithmic bytes (traffic grows in proportion to the states swept).  None once the
 # kernel has changed since the capture.
-SWEEP_DRAM_PER_ALG_BYTE = 298.148e6 / 251658120
+# arithmetic of each precision path (the per-state sweep work; FP64 always for the
+# layer scalars, the birth-death step and the residual)
+DTYPE = {"fp32+ir": "f32 sweeps + f64 refinement base", "fp32+df64": "f32 + df64 sweeps",
+         "fp32+fp64": "f32 + f64 sweeps", "fp64": "f64", "df64": "df64", "fp32": "f32"}
+SWEEP_DRAM_PER_ALG_BYTE = 298.587e6 / 251658120
 TRAFFIC_SOURCE = ("ncu --set full of one FP32 sweep at N=22 (profiles/k_persist_fp32_n22_set_full.md): "
-                  "298.1 MB DRAM for 251.7 MB algorithmic, scaled by algorithmic bytes")
+                  "298.6 MB DRAM for 251.7 MB algorithmic, scaled by algorithmic bytes")
 METRIC = ("state-updates/s (solve to 1e-10 relative balance residual; N=24 time-to-tol, "
           "FP32+refinement vs plain FP64, reported beside it)")
 BASE_SEED = {"n24": 3001, "n23": 3001, "n22": 3001, "n20": 2001, "n10": 1001}
@@ -62,7 +67,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="n24", choices=sorted(WORKLOADS))
-    ap.add_argument("--precision", default="fp32+df64")
+    ap.add_argument("--precision", default="fp32+ir")
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--omega", type=float, default=-1.0,
                     help="over-relaxation of the outer iteration: 1 = Algorithm 1 as printed, "
@@ -75,7 +80,8 @@ def parse():
     ap.add_argument("--warmstart", action="store_true",
                     help="learned warm start vs cold start on held-out N=16..22 instances (one JSON line)")
     ap.add_argument("--profile", action="store_true",
-                    help="one instance load and `--sweeps` DF64 sweeps, nothing else (for ncu)")
+                    help="one instance load and `--sweeps` sweeps in --precision (fp32, df64, "
+                         "fp64, or ir: correction sweeps after 4 FP32 sweeps), nothing else (for ncu)")
     ap.add_argument("--sweeps", type=int, default=2)
     return ap.parse_args()
 
@@ -93,9 +99,17 @@ def run_profile(args):
     s.load(torch.tensor(inst.lam_j, device=dev), torch.tensor(inst.nu, device=dev),
            torch.tensor(inst.pref, device=dev))
     torch.cuda.synchronize()
-    prec = args.precision if args.precision in ("fp32", "df64", "fp64") else "df64"
-    rc, st = s.solve(tol=0.0, tol_kind=hq.HQ_TOL_STEP, precision=prec, max_sweeps=args.sweeps,
-                     check_every=args.sweeps)
+    if args.precision == "ir":
+        # correction sweeps: a short FP32 solve, then one launch of `sweeps` correction
+        # sweeps against an FP64 base of its result (the second k_persist launch)
+        rc, st = s.solve(tol=0.0, tol_kind=hq.HQ_TOL_STEP, precision="fp32", max_sweeps=4,
+                         check_every=4)
+        hq.hq_profile_sweep(s.h, hq.HQ_PREC_FP32_IR, args.sweeps)
+        st["sweeps_hi"] = args.sweeps
+    else:
+        prec = args.precision if args.precision in ("fp32", "df64", "fp64") else "df64"
+        rc, st = s.solve(tol=0.0, tol_kind=hq.HQ_TOL_STEP, precision=prec, max_sweeps=args.sweeps,
+                         check_every=args.sweeps)
     s.close()
     print(json.dumps({"profile": inst.name, "sweeps": st["sweeps_hi"], "rc": rc}))
     return 0
@@ -359,7 +373,8 @@ def run_ours(args):
         if not args.no_compare and rank == 0:
             hq.hq_load(solver.h, lam_d, nu_d, pref_d)
             runs = (("fp64", "fp64", 1.0), ("df64", "df64", 1.0), ("fp32+df64", "fp32+df64", 1.0),
-                    ("fp64+sor", "fp64", -1.0), ("fp32+df64+sor", "fp32+df64", -1.0))
+                    ("fp32+ir", "fp32+ir", 1.0), ("fp64+sor", "fp64", -1.0),
+                    ("fp32+df64+sor", "fp32+df64", -1.0), ("fp32+ir+sor", "fp32+ir", -1.0))
             for name, pname, om in runs:
                 rc, st = hq.hq_solve(solver.h, opts(hq.PRECISION[pname], omega=om))
                 compare[name] = {"ms": round(st.ms_total, 3), "sweeps_fp32": st.sweeps_fp32,
@@ -369,7 +384,7 @@ def run_ours(args):
                 for name in compare:
                     compare[name]["speedup_vs_fp64"] = round(compare["fp64"]["ms"] / compare[name]["ms"], 3)
 
-        # ---- roofline of the DF64 sweep (the kernels that dominate the step) ------------------
+        # ---- roofline of the sweep kernel (the kernels that dominate the step) ----------------
         roof = None
         if rank == 0:
             hq.hq_load(solver.h, lam_d, nu_d, pref_d)
@@ -378,8 +393,8 @@ def run_ours(args):
             per_prec = {}
             # one launch of the persistent sweep kernel = `check_every` (8) sweeps, as in
             # the solve; timed with CUDA events on the solver's stream
-            for name, pc in (("fp32", hq.HQ_PREC_FP32), ("df64", hq.HQ_PREC_DF64),
-                             ("fp64", hq.HQ_PREC_FP64)):
+            for name, pc in (("fp32", hq.HQ_PREC_FP32), ("ir", hq.HQ_PREC_FP32_IR),
+                             ("df64", hq.HQ_PREC_DF64), ("fp64", hq.HQ_PREC_FP64)):
                 msw = min(hq.hq_profile_sweep(solver.h, pc, 8) for _ in range(3))
                 nbytes = hq.hq_sweep_bytes(solver.h, pc)
                 ach = nbytes / (msw / 1000.0) / 1e9
@@ -412,13 +427,13 @@ def run_ours(args):
         "metric": METRIC,
         "value": value, "unit": "state-updates/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32+df64 (fp64 scalars)",
+        "scaling": "weak", "vs_baseline": None, "dtype": DTYPE.get(args.precision, args.precision),
         "data": "synthetic",
         "config": {"workload": inst.name, "N": N, "J": J, "mode": I.MODE_NAMES[inst.mode],
                    "load": round(inst.load, 4), "tol": args.tol, "precision": args.precision,
                    "omega": "automatic" if args.omega < 0 else args.omega,
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
-                   "l2": "inputs larger than L2 (DF64 table 1.6 GB, FP32 table 0.8 GB)"},
+                   "l2": "inputs larger than L2 (FP64 table 1.6 GB, FP32 table 0.8 GB)"},
         "sweeps_per_step": {"fp32": st0["sweeps_fp32"], "hi": st0["sweeps_hi"]},
         "time_to_tol_ms": compare or None,
         "table_build_ms": st0["ms_table"],
@@ -447,7 +462,9 @@ def run_batch(args):
     stream = torch.cuda.Stream()
     solvers = [hq.Solver.for_instance(i, stream=stream) for i in insts]
     b = hq.hq_batch_create([s.h for s in solvers], stream=stream)
-    prec = hq.PRECISION[args.precision]
+    # correction sweeps are a single-instance mode: batched solves refine in DF64
+    bprec = "fp32+df64" if args.precision == "fp32+ir" else args.precision
+    prec = hq.PRECISION[bprec]
     tuned = {}
     for name, pc in (("fp32", hq.HQ_PREC_FP32), ("df64", hq.HQ_PREC_DF64), ("fp64", hq.HQ_PREC_FP64)):
         v, ms = hq.hq_batch_tune(b, pc, 4)
@@ -495,9 +512,9 @@ def run_batch(args):
                   "step tolerance), one persistent launch per check under a captured graph",
         "value": K / t_batch, "unit": "instances/s", "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1000 * t_batch, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": bprec, "data": "synthetic",
         "config": {"workload": f"batch{K}_n12_18_j200", "instances": K, "largest_N": int(info[1]),
-                   "states": int(info[2]), "tol_step": args.tol, "precision": args.precision,
+                   "states": int(info[2]), "tol_step": args.tol, "precision": bprec,
                    "omega": "automatic" if args.omega < 0 else args.omega},
         "state_updates_per_s": upd / t_batch, "converged": conv,
         "graph": {1: "captured graph replayed", -1: "capture refused: direct launches",

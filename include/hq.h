@@ -61,7 +61,13 @@ typedef enum {
                             48-bit significand, FP32 ALU */
   HQ_PREC_FP32 = 2,      /* FP32 sweeps only (accuracy ~1e-6 relative) */
   HQ_PREC_FP32_DF64 = 3, /* FP32 sweeps until they stall, then DF64 sweeps */
-  HQ_PREC_FP32_FP64 = 4  /* FP32 sweeps until they stall, then FP64 sweeps */
+  HQ_PREC_FP32_FP64 = 4, /* FP32 sweeps until they stall, then FP64 sweeps */
+  HQ_PREC_FP32_IR = 5    /* FP32 sweeps until they stall, then iterative refinement:
+                            FP32 sweeps of the correction e = p - p0 against an FP64
+                            base p0 (one FP64 pass over p0 per base; the base absorbs
+                            e and restarts when the correction's steps stall, at most
+                            3 times); the correction's FP32 rounding is relative to
+                            |e|, so the result is FP64-accurate */
 } hq_precision;
 
 typedef enum {
@@ -94,7 +100,8 @@ typedef struct hq_opts {
 
 typedef struct hq_stats {
   int sweeps_fp32;        /* sweeps done in FP32 */
-  int sweeps_hi;          /* sweeps done in FP64 or DF64 */
+  int sweeps_hi;          /* sweeps of the refinement phase (FP64, DF64 or FP32
+                             correction sweeps), or all sweeps of FP64 / DF64 solves */
   int residual_checks;    /* FP64 residual evaluations */
   int converged;          /* 1 if the tolerance was met */
   double final_step;      /* last max |p^k - p^{k-1}| */
@@ -103,7 +110,7 @@ typedef struct hq_stats {
   double ms_table;        /* wall time of the table build in the last hq_load */
   double state_updates;   /* (2^N - 2) * total sweeps */
   int warm_used;          /* 1 if a warm start was kept, 0 if cold (or fell back) */
-  int pad0;
+  int ir_bases;           /* HQ_PREC_FP32_IR: FP64 bases the refinement set up (0 otherwise) */
   double omega;           /* over-relaxation in use at the end of the solve */
   int reserved[2];
 } hq_stats;
@@ -177,8 +184,9 @@ int hq_get_table(hq_solver* h, double* T, uint32_t* masks, int mem);
 int hq_get_info(const hq_solver* h, int64_t* out8);
 
 /* Timing of the hot path: run `sweeps` outer iterations (Algorithm 1) of the current
- * iterate in precision `precision` (HQ_PREC_FP64 / HQ_PREC_DF64 / HQ_PREC_FP32;
- * the iterate is converted if needed) as one launch of the persistent sweep kernel,
+ * iterate in precision `precision` (HQ_PREC_FP64 / HQ_PREC_DF64 / HQ_PREC_FP32, or
+ * HQ_PREC_FP32_IR for correction sweeps; the iterate is converted if needed, a
+ * conversion to HQ_PREC_FP32_IR sets up a base) as one launch of the persistent sweep kernel,
  * with CUDA events on the solver's stream around it.  ms_out (host, 1 float)
  * receives the mean milliseconds per sweep.  The iterate advances by `sweeps`
  * iterations; call hq_solve again for results.  Needs a previous hq_solve. */
@@ -193,7 +201,8 @@ int hq_profile_phases(hq_solver* h, double* us_out, int max_out);
 
 /* Algorithmic HBM bytes of one outer iteration in `precision`: per state of
  * layers 1..N-1, its n table entries, r_m, its state mask, one read and one write
- * of p (neighbour layers are L2-resident and not counted).  Host double. */
+ * of p (neighbour layers are L2-resident and not counted); HQ_PREC_FP32_IR: an FP32
+ * correction sweep, which also reads six FP32 base terms per state.  Host double. */
 double hq_sweep_bytes(const hq_solver* h, int precision);
 
 /* Upward-rate table without any device allocation.  The paper has no
@@ -235,7 +244,8 @@ int hq_dispatch_table_static(int N, int J, const double* lambda_j, const int32_t
  *   floats) the ms per sweep of each variant.
  *   Untuned precisions use variant 0.  Overwrites the solvers' iterates.
  * hq_batch_solve: solves every instance cold to opts->tol on Algorithm 1's step
- *   (opts->tol_kind must be HQ_TOL_STEP; warm starts are not supported); precision,
+ *   (opts->tol_kind must be HQ_TOL_STEP; warm starts and HQ_PREC_FP32_IR are not
+ *   supported: HQ_EINVAL); precision,
  *   check_every, max_sweeps, fp32_stall and omega (per instance) as for hq_solve (a
  *   mixed precision leaves
  *   FP32 for every instance at once, when all have stalled).  Each check replays one

@@ -63,7 +63,7 @@ static void free_all(hq_solver* h) {
                   h->lidx, h->items, h->wfeat, h->wy, h->wlx,
                   h->b64.T, h->b64.r, h->b64.p, h->b64.nu, h->bdf.T, h->bdf.r, h->bdf.p, h->bdf.nu,
                   h->b32.T, h->b32.r, h->b32.p, h->b32.nu, h->ab, h->partials, h->sc, h->dflag,
-                  h->P, h->pn, h->rho, h->R, h->W, h->summary, h->pcond};
+                  h->P, h->pn, h->rho, h->R, h->W, h->summary, h->pcond, h->ir_base, h->ir, h->ir_part};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->hsc) cudaFreeHost(h->hsc);
@@ -164,6 +164,8 @@ extern "C" int hq_create(int N, int J, int mode, int capacity_C, void* stream, h
   HQ_TRY(dalloc(h, (double**)&h->b64.p, SP * 8));
   HQ_TRY(dalloc(h, (float2**)&h->bdf.p, SP * 8));
   HQ_TRY(dalloc(h, (float**)&h->b32.p, SP * 4));
+  HQ_TRY(dalloc(h, &h->ir_base, SP * 8));
+  HQ_TRY(dalloc(h, &h->ir, SP * 24));
   HQ_TRY(dalloc(h, (double**)&h->b64.nu, (int64_t)HQ_MAXN * 8));
   HQ_TRY(dalloc(h, (float2**)&h->bdf.nu, (int64_t)HQ_MAXN * 8));
   HQ_TRY(dalloc(h, (float**)&h->b32.nu, (int64_t)HQ_MAXN * 4));
@@ -193,10 +195,10 @@ extern "C" int hq_create(int N, int J, int mode, int capacity_C, void* stream, h
   {
     // padding entries are read by the bulk copies: give them defined (zero) contents
     void* zero_bufs[] = {h->masks, h->b64.T, h->b64.r, h->bdf.r, h->b32.r, h->b64.p, h->bdf.p,
-                         h->b32.p, h->ab};
+                         h->b32.p, h->ab, h->ir_base, h->ir};
     int64_t zero_len[] = {SP * 4, TE * 8, SP * 8, SP * 8, SP * 4, SP * 8, SP * 8, SP * 4,
-                          2 * h->ab_half_bytes};
-    for (int i = 0; i < 9 && e == cudaSuccess; i++)
+                          2 * h->ab_half_bytes, SP * 8, SP * 24};
+    for (int i = 0; i < 11 && e == cudaSuccess; i++)
       e = cudaMemsetAsync(zero_bufs[i], 0, (size_t)zero_len[i], h->stream);
   }
   if (e != cudaSuccess) {
@@ -207,6 +209,7 @@ extern "C" int hq_create(int N, int J, int mode, int capacity_C, void* stream, h
   }
   HQ_TRY(hq_build_layout(h));
   HQ_TRY(hq_build_items(h));
+  HQ_TRY(dalloc(h, &h->ir_part, (int64_t)(h->ifirst[N] > 0 ? h->ifirst[N] : 1) * 32));
   e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) {
     int rc = hq_cuda_fail(e, "layout build", __FILE__, __LINE__);
@@ -277,7 +280,7 @@ extern "C" int hq_solve(hq_solver* h, const hq_opts* opts_in, hq_stats* stats) {
   else hq_default_opts(&o);
   if (o.check_every < 1) o.check_every = 1;
   if (o.max_sweeps < 0) { hq_set_error("max_sweeps must be >= 0"); return HQ_EINVAL; }
-  if (o.precision < HQ_PREC_FP64 || o.precision > HQ_PREC_FP32_FP64) { hq_set_error("bad precision"); return HQ_EINVAL; }
+  if (o.precision < HQ_PREC_FP64 || o.precision > HQ_PREC_FP32_IR) { hq_set_error("bad precision"); return HQ_EINVAL; }
   if (o.tol_kind != HQ_TOL_STEP && o.tol_kind != HQ_TOL_RESIDUAL) { hq_set_error("bad tol_kind"); return HQ_EINVAL; }
   if (o.warm_start == HQ_WARM_GIVEN && !o.warm_p) { hq_set_error("warm_p is NULL"); return HQ_EINVAL; }
   if (o.warm_start == HQ_WARM_MLP && !h->mlp) { hq_set_error("no warm-start model is attached"); return HQ_EINVAL; }
@@ -298,8 +301,10 @@ extern "C" int hq_solve(hq_solver* h, const hq_opts* opts_in, hq_stats* stats) {
     case HQ_PREC_DF64: phases[0] = HQ_PREC_DF64; break;
     case HQ_PREC_FP32: phases[0] = HQ_PREC_FP32; break;
     case HQ_PREC_FP32_DF64: phases[0] = HQ_PREC_FP32; phases[1] = HQ_PREC_DF64; nph = 2; break;
+    case HQ_PREC_FP32_IR: phases[0] = HQ_PREC_FP32; phases[1] = HQ_PREC_IRC; nph = 2; break;
     default: phases[0] = HQ_PREC_FP32; phases[1] = HQ_PREC_FP64; nph = 2; break;
   }
+  int rebases = 0, ir_bases = 0;
   int ph = 0;
   int sweeps[2] = {0, 0};
   int total = 0, checks = 0, res_checks = 0, since_res = 0, stalled = 0;
@@ -383,6 +388,7 @@ extern "C" int hq_solve(hq_solver* h, const hq_opts* opts_in, hq_stats* stats) {
       if ((prev_check_step > 0.0 && ratio > stall) || step == 0.0) {
         rc = hq_convert_iterate(h, phases[ph], phases[ph + 1]);
         if (rc != HQ_OK) return rc;
+        if (phases[ph + 1] == HQ_PREC_IRC) ir_bases++;
         ph++;
         prev_check_step = 0.0;
         continue;
@@ -408,6 +414,17 @@ extern "C" int hq_solve(hq_solver* h, const hq_opts* opts_in, hq_stats* stats) {
       } else {
         since_res++;
       }
+    }
+    // correction sweeps whose steps stop shrinking have reached the FP32 floor of the
+    // correction: fold e into the base and start a new one (iterative refinement)
+    if (!converged && prec == HQ_PREC_IRC && prev_check_step > 0.0 && ratio > stall && rebases < 3) {
+      rc = hq_ir_begin(h, HQ_PREC_IRC);
+      if (rc != HQ_OK) return rc;
+      rebases++;
+      ir_bases++;
+      prev_check_step = 0.0;
+      stalled = 0;
+      continue;
     }
     // a precision floor that the tolerance lies below: stop instead of spinning
     if (!converged && prev_check_step > 0.0 && ratio >= 1.0) {
@@ -444,6 +461,7 @@ extern "C" int hq_solve(hq_solver* h, const hq_opts* opts_in, hq_stats* stats) {
     stats->ms_table = h->ms_table;
     stats->state_updates = (double)(h->S - 2) * (double)total;
     stats->warm_used = warm_kept ? 1 : 0;
+    stats->ir_bases = ir_bases;
     stats->omega = h->omega;
   }
   (void)checks;
@@ -551,9 +569,13 @@ extern "C" int hq_get_info(const hq_solver* h, int64_t* out8) {
 
 extern "C" double hq_sweep_bytes(const hq_solver* h, int precision) {
   if (!h) return 0.0;
-  const double e = precision == HQ_PREC_FP32 ? 4.0 : 8.0;
+  const bool ir = precision == HQ_PREC_FP32_IR;
+  const double e = (precision == HQ_PREC_FP32 || ir) ? 4.0 : 8.0;
+  // a correction sweep also reads six FP32 base terms per state (three in the gather,
+  // three in the finalisation)
+  const double extra = ir ? 24.0 : 0.0;
   double b = 0.0;
-  for (int n = 1; n <= h->N - 1; n++) b += (double)h->lsize[n] * ((n + 3) * e + 4.0);
+  for (int n = 1; n <= h->N - 1; n++) b += (double)h->lsize[n] * ((n + 3) * e + 4.0 + extra);
   return b;
 }
 
@@ -561,12 +583,14 @@ extern "C" int hq_profile_sweep(hq_solver* h, int precision, int sweeps, float* 
   int rc = need_solved(h);
   if (rc != HQ_OK) return rc;
   if (!ms_out || sweeps < 1) { hq_set_error("ms_out NULL or sweeps < 1"); return HQ_EINVAL; }
-  if (precision != HQ_PREC_FP64 && precision != HQ_PREC_DF64 && precision != HQ_PREC_FP32) {
-    hq_set_error("precision must be FP64, DF64 or FP32");
+  if (precision != HQ_PREC_FP64 && precision != HQ_PREC_DF64 && precision != HQ_PREC_FP32 &&
+      precision != HQ_PREC_FP32_IR) {
+    hq_set_error("precision must be FP64, DF64, FP32 or FP32_IR");
     return HQ_EINVAL;
   }
   ms_out[0] = 0.f;
   if (h->N < 2) return HQ_OK;
+  if (precision == HQ_PREC_FP32_IR) precision = HQ_PREC_IRC;  // correction sweeps
   if (h->cur_prec != precision) {
     rc = hq_convert_iterate(h, h->cur_prec, precision);
     if (rc != HQ_OK) return rc;

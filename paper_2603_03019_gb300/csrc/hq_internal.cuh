@@ -176,6 +176,11 @@ struct DevScalars {
   double fac[HQ_MAXN + 1];     // P{B} = fac[w(B)] * p_w(B) after the birth-death step
   double lam;                  // lambda = sum_j lambda_j of the loaded instance
   double pub[2][8];            // per-phase results published at the persistent kernel's barrier
+  // refinement (correction sweeps against an FP64 base p0): the base's layer scalars
+  // c1^0(n), c2^0(n) and its per-layer sums {sum mu A0, sum mu B0, sum A0, sum B0}
+  double ir_c1[HQ_MAXN + 1];
+  double ir_c2[HQ_MAXN + 1];
+  double ir_sum[4][HQ_MAXN + 1];
   unsigned long long t_start;  // %globaltimer at the start of the last sweep launch (ns)
   unsigned long long t_phase[64];  // %globaltimer at the release of phase g of that launch
 };
@@ -255,6 +260,12 @@ struct hq_solver {
   double ms_table = 0;
   // learned warm start: attached model (borrowed) and scratch
   hq_mlp* mlp = nullptr;
+  // refinement: the FP64 base p0 (layer-ranked, Sp) and 6 x Sp FP32 per-state base terms
+  // {rho0, A0, B0, G_rho, G_A, G_B}; the iterate of the correction sweeps is e = p - p0,
+  // held in b32.p; ir_part: 4 FP64 partial sums per work item of the base pass
+  double* ir_base = nullptr;
+  float* ir = nullptr;
+  double* ir_part = nullptr;
   float* wfeat = nullptr;      // N (N-1) rows x HQ_MLP_FEATURES: (layer n, unit i) pairs
   float* wy = nullptr;         // N (N-1) predictions (logit q_i(n))
   double* wlx = nullptr;       // log x_i(n) [HQ_MAXN^2], log e_n [HQ_MAXN + 1]
@@ -274,6 +285,13 @@ int hq_build_rates(hq_solver* h);  // r_m in all precisions
 int hq_mlp_predict_dev(hq_mlp* m, const float* X, int B, float* y_dev, cudaStream_t s);
 int hq_mlp_features_dev(hq_solver* h, float* X);
 int hq_mlp_warm_start(hq_solver* h, hq_mlp* m, double* P, double* rho);
+
+// refinement (hq_refine.cu): correction sweeps run as sweep precision HQ_PREC_IRC on
+// the FP32 buffers; hq_ir_begin sets up a base from the iterate held in precision
+// `from` (from == HQ_PREC_IRC: re-base on p0 + e), hq_ir_assemble writes p0 + e to b64.p
+#define HQ_PREC_IRC 16
+int hq_ir_begin(hq_solver* h, int from);
+int hq_ir_assemble(hq_solver* h);
 
 // work items and low-part positions of the sweep (hq_items.cu)
 int hq_item_list(int N, std::vector<uint4>& items, int* ifirst);  // host list, layer by layer

@@ -79,9 +79,10 @@ struct PersistArgs {
   void* ab1;
   double* partials;  // [2][gridDim][kPW]
   DevScalars* sc;
+  const float* ir;   // correction sweeps: 6 x Sp base terms {rho0, A0, B0, G_rho, G_A, G_B}
 };
 
-template <class V, bool kFullL>
+template <class V, bool kFullL, bool kIR>
 __global__ void __launch_bounds__(kThreads, 1) k_persist(PersistArgs a) {
   typedef typename V::T T;
   typedef Pair<V> PR;
@@ -97,6 +98,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_persist(PersistArgs a) {
   __shared__ T s_hnu[kWarps][32];        // and its idle high-part units' rates
   __shared__ T s_lamT, s_one;
   __shared__ T s_c1, s_c2;
+  __shared__ T s_d1, s_d2;  // correction sweeps: c1 - c1^0, c2 - c2^0 of the last layer solved
   __shared__ double s_step[2];
   __shared__ int s_last;
   __shared__ unsigned s_gen0;
@@ -129,6 +131,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_persist(PersistArgs a) {
     s_one = V::from_d(1.0);
     s_c1 = V::zero();
     s_c2 = V::zero();
+    s_d1 = V::zero();
+    s_d2 = V::zero();
     s_step[0] = s_step[1] = 0.0;
     if (blockIdx.x == 0) sc->t_start = globaltimer_ns();
     // no barrier of this launch completes before every CTA has arrived once
@@ -144,12 +148,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_persist(PersistArgs a) {
   const int nwarps = (int)G * kWarps;
   int gphase = 0;  // phase counter within this launch
 
-  // finalise layer lf from the (A, B) buffer `abf`: p = c1 A + c2 B, |p - p_old|
+  // finalise layer lf from the (A, B) buffer `abf`: p = c1 A + c2 B, |p - p_old|; in
+  // correction sweeps e = rho0 + d1 A0 + d2 B0 + c1 a + c2 b (the pairs hold a, b)
   auto finalize = [&](int lf, const P2* abf, float& md) {
-    const T c1 = s_c1, c2 = s_c2;
+    const T c1 = s_c1, c2 = s_c2, d1 = s_d1, d2 = s_d2;
     const bool relax = a.omega != 1.0;
     const T om = V::from_d(a.omega);
     T* pl = pw + a.off[lf];
+    const T* r0 = kIR ? (const T*)(a.ir + a.off[lf]) : nullptr;
     const int64_t Lf = a.lsize[lf];
     const int64_t nthreads = (int64_t)G * blockDim.x;
 #pragma unroll 4
@@ -157,6 +163,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_persist(PersistArgs a) {
       const P2 q = ld_l2(abf + k);
       const T old = ld_l2(pl + k);
       T v = V::add(V::mul(c1, PR::A(q)), V::mul(c2, PR::B(q)));
+      if constexpr (kIR) {
+        const T base = V::add(ld_stream(r0 + k),
+                              V::add(V::mul(d1, ld_stream(r0 + a.Sp + k)), V::mul(d2, ld_stream(r0 + 2 * a.Sp + k))));
+        v = V::add(base, v);
+      }
       if (relax) v = V::add(old, V::mul(om, V::sub(v, old)));
       md = fmaxf(md, V::absdiff(v, old));
       pl[k] = v;
@@ -223,6 +234,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_persist(PersistArgs a) {
 #pragma unroll
         for (int w = 0; w < 5; w++) f[w] = s_red[w][0];
         double* pub = sc->pub[buf];
+        if (kIR && lg > 0) {
+          // the correction sums plus the base's: the sums of the full (A, B) of layer lg
+#pragma unroll
+          for (int w = 0; w < 4; w++) f[w] += sc->ir_sum[w][lg];
+        }
         if (lg > 0) {
           // closed-form limit of the inner loop (Eq. 12 and 14), then Eq. (13)
           const double alpha = 1.0 / s_lam[lg - 1];
@@ -234,6 +250,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_persist(PersistArgs a) {
           pub[1] = beta;
           pub[2] = a.lam * (c1 * f[2] + beta * f[3]);
           pub[3] = mustar;
+          pub[5] = c1 - sc->ir_c1[lg];
+          pub[6] = beta - sc->ir_c2[lg];
+          sc->c1[lg] = c1;
+          sc->c2[lg] = beta;
           if (!isfinite(mustar) || !(aa < 1.0)) atomicOr(&sc->flags, 1);
         }
         pub[4] = f[4];
@@ -258,6 +278,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_persist(PersistArgs a) {
       if (lg > 0) {
         s_c1 = V::from_d(__ldcg(pub + 0));
         s_c2 = V::from_d(__ldcg(pub + 1));
+        if (kIR) {
+          s_d1 = V::from_d(__ldcg(pub + 5));
+          s_d2 = V::from_d(__ldcg(pub + 6));
+        }
         s_lam[lg] = __ldcg(pub + 2);
         s_mu[lg] = __ldcg(pub + 3);
       }
@@ -301,14 +325,19 @@ __global__ void __launch_bounds__(kThreads, 1) k_persist(PersistArgs a) {
       lv.c2 = s_c2;
       lv.lamT = s_lamT;
       lv.one = s_one;
+      lv.gR = kIR ? a.ir + 3 * a.Sp : nullptr;
+      lv.gA = kIR ? a.ir + 4 * a.Sp : nullptr;
+      lv.gB = kIR ? a.ir + 5 * a.Sp : nullptr;
+      lv.d1 = s_d1;
+      lv.d2 = s_d2;
       const int it_end = a.ifirst[n + 1];
       int it = a.ifirst[n] + gwarp;
       uint4 dnext = it < it_end ? __ldg(a.items + it) : make_uint4(0u, 0u, 0u, 0u);
       for (; it < it_end; it += nwarps) {
         const uint4 d = dnext;
         if (it + nwarps < it_end) dnext = __ldg(a.items + it + nwarps);  // next item, ahead
-        gather_item<V, kFullL>(lv, d, s_RL, s_binL, slot_d, slot_u, s_hl[wid], s_hnu[wid], lane, sA, sB,
-                               sa, sb);
+        gather_item<V, kFullL, kIR>(lv, d, s_RL, s_binL, slot_d, slot_u, s_hl[wid], s_hnu[wid], lane, sA,
+                                    sB, sa, sb);
         __syncwarp();  // the slot and the lists are rewritten by the next item
       }
       sync_phase(sA, sB, sa, sb, md, n, n >= 2 ? k : k - 1);
@@ -333,17 +362,23 @@ __global__ void __launch_bounds__(kThreads, 1) k_persist(PersistArgs a) {
   }
 }
 
-int g_occ[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+int g_occ[4][2] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
 int g_nsm = 0;
 
+template <class V, bool kIR>
+const void* persist_fn(bool full) {
+  return full ? (const void*)k_persist<V, true, kIR> : (const void*)k_persist<V, false, kIR>;
+}
+
+// ir: correction sweeps (FP32 only), against the base set up by hq_ir_begin
 template <class V>
-int launch_persist(hq_solver* h, int nsweeps, cudaEvent_t ev0, cudaEvent_t ev1) {
+int launch_persist(hq_solver* h, int nsweeps, cudaEvent_t ev0, cudaEvent_t ev1, bool ir = false) {
   typedef typename V::T T;
   typedef typename Pair<V>::P P2;
-  const int slot = V::kind == HQ_PREC_FP64 ? 0 : (V::kind == HQ_PREC_DF64 ? 1 : 2);
+  const int slot = ir ? 3 : (V::kind == HQ_PREC_FP64 ? 0 : (V::kind == HQ_PREC_DF64 ? 1 : 2));
   const size_t smem = (size_t)kWarps * Slot<V>::kBytes;
   const bool full = h->L == HQ_LO_BITS;
-  const void* kfn = full ? (const void*)k_persist<V, true> : (const void*)k_persist<V, false>;
+  const void* kfn = ir ? persist_fn<PolF32, true>(full) : persist_fn<V, false>(full);
   if (!g_nsm) HQ_CUDA(cudaDeviceGetAttribute(&g_nsm, cudaDevAttrMultiProcessorCount, h->dev));
   if (!g_occ[slot][full]) {
     HQ_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -396,6 +431,7 @@ int launch_persist(hq_solver* h, int nsweeps, cudaEvent_t ev0, cudaEvent_t ev1) 
   a.ab1 = (char*)h->ab + h->ab_half_bytes;
   a.partials = h->partials;
   a.sc = h->sc;
+  a.ir = ir ? h->ir : nullptr;
   void* args[] = {&a};
   // a barrier left half-entered by an aborted launch must not leak into this one
   HQ_CUDA(cudaMemsetAsync(&h->sc->bar_count, 0, sizeof(unsigned), h->stream));
@@ -425,6 +461,7 @@ int hq_run_sweeps(hq_solver* h, int prec, int nsweeps, cudaEvent_t ev0, cudaEven
     int rc;
     if (prec == HQ_PREC_FP64) rc = launch_persist<PolF64>(h, k, e0, e1);
     else if (prec == HQ_PREC_DF64) rc = launch_persist<PolDF>(h, k, e0, e1);
+    else if (prec == HQ_PREC_IRC) rc = launch_persist<PolF32>(h, k, e0, e1, true);
     else rc = launch_persist<PolF32>(h, k, e0, e1);
     if (rc != HQ_OK) return rc;
     done += k;

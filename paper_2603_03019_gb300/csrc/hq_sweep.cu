@@ -106,6 +106,15 @@ __global__ void k_f32_to_df(int64_t S, const float* src, float2* dst) {
 
 int hq_convert_iterate(hq_solver* h, int from, int to) {
   if (from == to) return HQ_OK;
+  if (to == HQ_PREC_IRC) return hq_ir_begin(h, from);
+  if (from == HQ_PREC_IRC) {
+    // the refinement's iterate is p0 + e: assemble it in FP64 first
+    const int rc = hq_ir_assemble(h);
+    if (rc != HQ_OK) return rc;
+    h->cur_prec = HQ_PREC_FP64;
+    if (to == HQ_PREC_FP64) return HQ_OK;
+    from = HQ_PREC_FP64;
+  }
   const int64_t S = h->Sp;
   unsigned grid = (unsigned)((S + 255) / 256);
   void* s = hq_bufs(h, from).p;

@@ -110,6 +110,12 @@ template <class V> struct LayerView {
   const T* nu;        // nu_i in this precision
   T c1, c2;           // p_{n-1} = c1 A + c2 B
   T lamT, one;
+  // correction sweeps (refinement): the pull gathers of the base terms of layer n-1
+  // (G_rho, G_A, G_B at off_n + rank) and d1 = c1 - c1^0, d2 = c2 - c2^0 of layer n-1
+  const float* gR;
+  const float* gA;
+  const float* gB;
+  T d1, d2;
 };
 
 // Gather one item of layer n (Eq. 12): A_m = r_m sum_s p_{n-1}(m - c_s) T[m][s] with
@@ -124,9 +130,12 @@ template <class V> struct LayerView {
 // block of layer n+1).  High part: counted loops over the warp's list `hl` of neighbour
 // block bases (the item's busy units first, then its idle units, each increasing) with
 // the idle units' rates in `hnu`; every lane reads the same entry.  kFullL: L equals
-// HQ_LO_BITS (every instance with N >= HQ_LO_BITS).  The caller syncs the warp before the
-// slot and the lists are rewritten by the next item.
-template <class V, bool kFullL>
+// HQ_LO_BITS (every instance with N >= HQ_LO_BITS).  kIR (FP32 only): the pairs and p
+// are the corrections a, b, e against a fixed base, and the pull term gains the base's
+// part G_rho + d1 G_A + d2 G_B (layer 1 pulls nothing: the empty state has no
+// correction).  The caller syncs the warp before the slot and the lists are rewritten
+// by the next item.
+template <class V, bool kFullL, bool kIR = false>
 __device__ __forceinline__ void gather_item(const LayerView<V>& lv, const uint4 d, const uint32_t* s_RL,
                                             const int* s_binL, unsigned char* slot_d,
                                             unsigned char* slot_u, uint32_t* hl, typename V::T* hnu,
@@ -164,6 +173,14 @@ __device__ __forceinline__ void gather_item(const LayerView<V>& lv, const uint4 
   const uint32_t iw0 = __ldg(lv.lidx + gi), iw1 = __ldg(lv.lidx + lv.Sp + gi),
                  iw2 = __ldg(lv.lidx + 2 * lv.Sp + gi);
   const T rv = __ldg(lv.rt + gi);
+  T g0 = V::zero(), g1 = V::zero(), g2 = V::zero();
+  if constexpr (kIR) {
+    if (pull) {
+      g0 = ld_stream(lv.gR + gi);
+      g1 = ld_stream(lv.gA + gi);
+      g2 = ld_stream(lv.gB + gi);
+    }
+  }
   const T* tcol = lv.Tt + lv.toff_n + kq;  // table slot s at tcol[s * lp]
   const int64_t lp = lv.lp;
   // table entries of the low-part busy neighbours, issued before the staging wait
@@ -231,7 +248,14 @@ __device__ __forceinline__ void gather_item(const LayerView<V>& lv, const uint4 
 #pragma unroll 4
   for (int k = 0; k < nih; k++) V::fma_acc(D, ld_l2(lv.p_up + hl[nbh + k] + rl), hnu[k]);
   // up-inflow: layer 0 is the empty state with p_0 = 1
-  const T U = pull ? V::add(V::mul(lv.c1, V::norm(UA)), V::mul(lv.c2, V::norm(UB))) : ld_stream(tcol);
+  T U;
+  if constexpr (kIR) {
+    U = pull ? V::add(V::add(g0, V::add(V::mul(lv.d1, g1), V::mul(lv.d2, g2))),
+                      V::add(V::mul(lv.c1, UA), V::mul(lv.c2, UB)))
+             : V::zero();
+  } else {
+    U = pull ? V::add(V::mul(lv.c1, V::norm(UA)), V::mul(lv.c2, V::norm(UB))) : ld_stream(tcol);
+  }
   D = V::norm(D);
   const T qm = V::sub(lv.one, V::mul(lv.lamT, rv));  // mu_m r_m = 1 - lambda r_m
   const T A = V::mul(U, rv), B = V::mul(D, rv);

@@ -19,12 +19,12 @@ HQ_OK, HQ_EINVAL, HQ_ENOMEM, HQ_EUNSTABLE, HQ_ENOTCONVERGED = 0, -1, -2, -3, -4
 HQ_EDIVERGED, HQ_ETIMEOUT, HQ_ECUDA, HQ_ESTATE = -5, -6, -7, -8
 HQ_LOSS, HQ_FINITE, HQ_INFINITE = 0, 1, 2
 HQ_HOST, HQ_DEVICE = 0, 1
-HQ_PREC_FP64, HQ_PREC_DF64, HQ_PREC_FP32, HQ_PREC_FP32_DF64, HQ_PREC_FP32_FP64 = 0, 1, 2, 3, 4
+HQ_PREC_FP64, HQ_PREC_DF64, HQ_PREC_FP32, HQ_PREC_FP32_DF64, HQ_PREC_FP32_FP64, HQ_PREC_FP32_IR = 0, 1, 2, 3, 4, 5
 HQ_TOL_STEP, HQ_TOL_RESIDUAL = 0, 1
 HQ_WARM_NONE, HQ_WARM_GIVEN, HQ_WARM_MLP = 0, 1, 2
 
 PRECISION = {"fp64": HQ_PREC_FP64, "df64": HQ_PREC_DF64, "fp32": HQ_PREC_FP32,
-             "fp32+df64": HQ_PREC_FP32_DF64, "fp32+fp64": HQ_PREC_FP32_FP64}
+             "fp32+df64": HQ_PREC_FP32_DF64, "fp32+fp64": HQ_PREC_FP32_FP64, "fp32+ir": HQ_PREC_FP32_IR}
 
 
 class hq_opts(ctypes.Structure):
@@ -41,10 +41,10 @@ class hq_stats(ctypes.Structure):
                 ("final_step", ctypes.c_double), ("final_residual", ctypes.c_double),
                 ("ms_total", ctypes.c_double), ("ms_table", ctypes.c_double),
                 ("state_updates", ctypes.c_double), ("warm_used", ctypes.c_int),
-                ("pad0", ctypes.c_int), ("omega", ctypes.c_double), ("reserved", ctypes.c_int * 2)]
+                ("ir_bases", ctypes.c_int), ("omega", ctypes.c_double), ("reserved", ctypes.c_int * 2)]
 
     def as_dict(self) -> dict:
-        return {k: getattr(self, k) for k, _ in self._fields_ if k not in ("reserved", "pad0")}
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
 
 
 class HQError(RuntimeError):

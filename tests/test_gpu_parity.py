@@ -88,7 +88,7 @@ CASES = [(6, 9, 0, 0, 11), (10, 50, 0, 0, 12), (9, 33, 1, 4, 13), (10, 41, 2, 0,
          (13, 80, 0, 0, 15), (13, 64, 2, 0, 16)]
 
 
-@pytest.mark.parametrize("prec", ["fp64", "df64", "fp32+df64", "fp32+fp64"])
+@pytest.mark.parametrize("prec", ["fp64", "df64", "fp32+df64", "fp32+fp64", "fp32+ir"])
 @pytest.mark.parametrize("N,J,mode,C,seed", CASES)
 def test_solve_matches_oracle(gpu_lib, N, J, mode, C, seed, prec):
     inst = I.geometric_instance(N, J, seed, 0.7, nu_lo=0.5, nu_hi=1.5, mode=mode, C=C)
@@ -233,10 +233,11 @@ def test_mixed_n20_against_oracle(gpu_lib):
 
 # ---- full size: N=24, J=1000 infinite queue, the benchmark's launch configuration --------
 
-def test_large_n24_sampled(gpu_lib):
+@pytest.mark.parametrize("prec", ["fp32+df64", "fp32+ir"])
+def test_large_n24_sampled(gpu_lib, prec):
     inst = I.large_infinite_n24()
     s = hq.Solver.for_instance(inst)
-    rc, st = s.solve(tol=1e-10, precision="fp32+df64")
+    rc, st = s.solve(tol=1e-10, precision=prec, omega=-1.0)
     assert rc == hq.HQ_OK, st
     P = s.stationary()
     T, masks = s.table()
@@ -284,7 +285,8 @@ def test_large_n24_sampled(gpu_lib):
 
 # ---- over-relaxation (not in the paper): same fixed point, fewer sweeps ------------------
 
-@pytest.mark.parametrize("prec,omega", [("fp64", -1.0), ("fp32+df64", -1.0), ("df64", 1.3)])
+@pytest.mark.parametrize("prec,omega", [("fp64", -1.0), ("fp32+df64", -1.0), ("df64", 1.3),
+                                        ("fp32+ir", -1.0)])
 @pytest.mark.parametrize("N,J,mode,C,seed", CASES)
 def test_relaxed_solve_matches_oracle(gpu_lib, N, J, mode, C, seed, prec, omega):
     inst = I.geometric_instance(N, J, seed, 0.7, nu_lo=0.5, nu_hi=1.5, mode=mode, C=C)
@@ -311,3 +313,36 @@ def test_relaxation_saves_sweeps_and_rejects_bad_omega(gpu_lib):
             s.solve(tol=1e-10, precision="fp64", omega=bad)
         assert e.value.code == hq.HQ_EINVAL
     s.close()
+
+
+# ---- iterative refinement (not in the paper): FP32 corrections against an FP64 base --------
+
+def test_refinement_matches_fp64_and_rebases(gpu_lib):
+    """FP32 correction sweeps reach the FP64 fixed point: the refined N=20 solution agrees
+    with plain FP64 sweeps and the oracle; a stall threshold that declares every check
+    stalled forces the base to absorb the correction repeatedly (3 re-bases, the cap)."""
+    inst = I.mixed_n20(2001, 0.6)
+    s = hq.Solver.for_instance(inst)
+    rc, ref = s.solve(tol=1e-13, precision="fp64", omega=-1.0)
+    assert rc == hq.HQ_OK
+    P64, rho64 = s.stationary(), s.utilisation()
+    rc, st = s.solve(tol=1e-13, precision="fp32+ir", omega=-1.0)
+    assert rc == hq.HQ_OK, st
+    assert st["ir_bases"] >= 1 and st["sweeps_hi"] > 0 and st["sweeps_fp32"] > 0
+    assert st["final_residual"] < 1e-13
+    # rho sums 2^19 states: both solves' residuals (1e-13) times the chain's
+    # relaxation factor (~1e2) each
+    assert np.max(np.abs(s.stationary() - P64)) < 1e-11
+    assert np.max(np.abs(s.utilisation() - rho64)) < 1e-10
+    # early switches and re-bases leave the last base far from the solution, so the
+    # tolerance may lie below what its correction can reach: accept the floor stop
+    rc, st2 = s.solve(tol=1e-13, precision="fp32+ir", fp32_stall=1e-3, max_sweeps=800)
+    assert rc in (hq.HQ_OK, hq.HQ_ENOTCONVERGED), st2
+    assert st2["ir_bases"] == 4
+    assert np.max(np.abs(s.stationary() - P64)) < 1e-10
+    r = oracle.solve(inst, eps=1e-15)
+    assert np.max(np.abs(P64 - r["P"])) < 1e-10
+    ms = hq.hq_profile_sweep(s.h, hq.HQ_PREC_FP32_IR, 2)
+    assert ms > 0
+    s.close()
+
