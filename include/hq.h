@@ -87,7 +87,9 @@ typedef struct hq_opts {
   int warm_mem;        /* hq_mem of warm_p */
   const double* warm_p;/* HQ_WARM_GIVEN: start vector p_n(B) in y-order, length 2^N */
   double fp32_stall;   /* mixed modes: leave FP32 when the step's decay per check is
-                          worse than this ratio (0 = default 0.9) */
+                          worse than this ratio (0 = default 0.9); HQ_PREC_FP32_IR
+                          also re-bases when four checks in a row decay worse than it,
+                          or one does after the correction shrank by 1e4 */
   double omega;        /* over-relaxation of the outer iteration (not in the paper):
                           each finalised layer becomes p_old + omega (p_new - p_old);
                           0 or 1 = Algorithm 1 as printed; (1, 2) fixed; negative =

@@ -304,7 +304,8 @@ extern "C" int hq_solve(hq_solver* h, const hq_opts* opts_in, hq_stats* stats) {
     case HQ_PREC_FP32_IR: phases[0] = HQ_PREC_FP32; phases[1] = HQ_PREC_IRC; nph = 2; break;
     default: phases[0] = HQ_PREC_FP32; phases[1] = HQ_PREC_FP64; nph = 2; break;
   }
-  int rebases = 0, ir_bases = 0;
+  int rebases = 0, ir_bases = 0, ir_flat = 0;
+  double step_base = 0.0;  // the first step of the current refinement base
   int ph = 0;
   int sweeps[2] = {0, 0};
   int total = 0, checks = 0, res_checks = 0, since_res = 0, stalled = 0;
@@ -416,15 +417,24 @@ extern "C" int hq_solve(hq_solver* h, const hq_opts* opts_in, hq_stats* stats) {
       }
     }
     // correction sweeps whose steps stop shrinking have reached the FP32 floor of the
-    // correction: fold e into the base and start a new one (iterative refinement)
-    if (!converged && prec == HQ_PREC_IRC && prev_check_step > 0.0 && ratio > stall && rebases < 3) {
-      rc = hq_ir_begin(h, HQ_PREC_IRC);
-      if (rc != HQ_OK) return rc;
-      rebases++;
-      ir_bases++;
-      prev_check_step = 0.0;
-      stalled = 0;
-      continue;
+    // correction: fold e into the base and start a new one (iterative refinement).  A
+    // flat check is a floor once the correction has shrunk by 1e4; before that only four
+    // flat checks in a row are (over-relaxed sweeps pause for a check or two on their way
+    // down, and a new base costs about five sweeps).
+    if (prec == HQ_PREC_IRC) {
+      if (step_base == 0.0) step_base = step;
+      ir_flat = (prev_check_step > 0.0 && ratio > stall) ? ir_flat + 1 : 0;
+      if (!converged && rebases < 3 && (ir_flat >= 4 || (ir_flat >= 1 && step < 1e-4 * step_base))) {
+        rc = hq_ir_begin(h, HQ_PREC_IRC);
+        if (rc != HQ_OK) return rc;
+        rebases++;
+        ir_bases++;
+        ir_flat = 0;
+        step_base = 0.0;
+        prev_check_step = 0.0;
+        stalled = 0;
+        continue;
+      }
     }
     // a precision floor that the tolerance lies below: stop instead of spinning
     if (!converged && prev_check_step > 0.0 && ratio >= 1.0) {
