@@ -672,7 +672,10 @@ extern "C" int hq_batch_tune(hq_batch* b, int precision, int sweeps, int* varian
   }
   b->variant[slot_of(precision)] = best;
   if (variant_out) *variant_out = best;
-  for (hq_solver* h : b->s) h->cur_prec = precision;
+  for (hq_solver* h : b->s) {
+    h->cur_prec = precision;
+    h->it_version++;
+  }
   return HQ_OK;
 }
 
@@ -788,7 +791,10 @@ extern "C" int hq_batch_solve(hq_batch* b, const hq_opts* opts_in, hq_stats* sta
     HQ_CUDA(cudaMemcpyAsync(b->omega, om.data(), sizeof(double) * K, cudaMemcpyHostToDevice, b->stream));
   }
   HQ_CUDA(cudaStreamSynchronize(b->stream));
-  for (hq_solver* h : b->s) h->cur_prec = phases[ph];
+  for (hq_solver* h : b->s) {
+    h->cur_prec = phases[ph];
+    h->it_version++;  // the batched kernel moved every iterate
+  }
   std::vector<double> res(K, -1.0);
   if (status == HQ_OK) {
     int c = 0;

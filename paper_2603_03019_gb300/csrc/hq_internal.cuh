@@ -167,7 +167,7 @@ struct DevScalars {
   int flags;                   // bit 0: non-finite value seen
   unsigned ticket[4];          // last-block tickets
   unsigned bar_count;          // grid barrier of the persistent sweep kernel: arrivals
-  unsigned bar_gen;            // grid barrier: generation
+  unsigned bar_gen;            // (unused; kept for the layout)
   double red[16];              // results of whole-vector reductions
   double lsum[HQ_MAXN + 1];    // sum_m p_n(B_m) per layer (whole-vector pass)
   double lmu[HQ_MAXN + 1];     // sum_m mu_m p_n(B_m) per layer
@@ -175,7 +175,7 @@ struct DevScalars {
   double res_den[HQ_MAXN + 1]; // max_m out_m per layer
   double fac[HQ_MAXN + 1];     // P{B} = fac[w(B)] * p_w(B) after the birth-death step
   double lam;                  // lambda = sum_j lambda_j of the loaded instance
-  double pub[2][8];            // per-phase results published at the persistent kernel's barrier
+  double pub[2][8];            // (unused; kept for the layout)
   // refinement (correction sweeps against an FP64 base p0): the base's layer scalars
   // c1^0(n), c2^0(n) and its per-layer sums {sum mu A0, sum mu B0, sum A0, sum B0}
   double ir_c1[HQ_MAXN + 1];
@@ -228,6 +228,9 @@ struct hq_solver {
   bool loaded = false, solved = false;
   int cur_prec = -1;           // precision holding the current iterate
   double omega = 1.0;          // over-relaxation of the finalised layers (1: Algorithm 1)
+  // every change of the iterate bumps it_version; res_version is the version whose FP64
+  // residual, layer law and summary the last residual pass computed
+  uint64_t it_version = 1, res_version = 0;
 
   // N-dependent layout
   uint32_t* masks = nullptr;   // S, layer-ranked state masks

@@ -20,10 +20,11 @@
 // p_{n-1} = c1 A + c2 B on the fly (accumulating sum T A and sum T B separately), and
 // phase n also writes the final p_{n-1} and its step |p^k - p^{k-1}|.  One grid
 // barrier per layer; layer N-1 of sweep k is finalised in phase 1 of sweep k+1 (which
-// does not read it), and a closing phase finalises the last sweep.  The CTA that
-// arrives last at a barrier folds every CTA's partial sums in a fixed order, solves
-// the layer's scalar recursion and publishes c1, c2, lambda(n), mu(n) and the step
-// before it releases the others: the result is deterministic.
+// does not read it), and a closing phase finalises the last sweep.  Once every CTA has
+// arrived at a barrier, each CTA folds all CTAs' partial sums in the same fixed order
+// and solves the layer's scalar recursion (c1, c2, lambda(n), mu(n), the step) itself:
+// the result is deterministic and identical in every CTA, and no CTA waits for another
+// to publish it.
 //
 // Work.  Layer n is cut into items of at most 32 consecutive states of one rank block
 // (see HQ_ITEM_HI_BITS); items go round-robin to the warps of the grid.  A warp first
@@ -100,8 +101,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_persist(PersistArgs a) {
   __shared__ T s_c1, s_c2;
   __shared__ T s_d1, s_d2;  // correction sweeps: c1 - c1^0, c2 - c2^0 of the last layer solved
   __shared__ double s_step[2];
-  __shared__ int s_last;
-  __shared__ unsigned s_gen0;
+  __shared__ double s_alpha, s_beta;  // 1/lambda(n-1) and lambda(n)/mu(n+1) of the layer solved
 
   DevScalars* sc = a.sc;
   const int N = a.N, L = a.L, H = a.H;
@@ -135,8 +135,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_persist(PersistArgs a) {
     s_d2 = V::zero();
     s_step[0] = s_step[1] = 0.0;
     if (blockIdx.x == 0) sc->t_start = globaltimer_ns();
-    // no barrier of this launch completes before every CTA has arrived once
-    s_gen0 = ld_relaxed_u32(&sc->bar_gen);
   }
   __syncthreads();
 
@@ -175,11 +173,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_persist(PersistArgs a) {
   };
 
   // Write this CTA's partials, then the grid barrier.  Arrivals count up on bar_count
-  // (zeroed before the launch): the CTA whose arrival completes phase g's count folds
-  // all partials in CTA order, solves the scalar recursion of layer lg (if lg > 0),
-  // publishes the result and then bumps bar_gen with release semantics; the others wait
-  // for bar_gen to reach gen0 + g + 1.  ks: sweep of the layer finalised in this phase
-  // (its step goes into s_step).
+  // (zeroed before the launch, released by the arriving thread so that its partials are
+  // visible); phase g completes when the count reaches G (g + 1).  Then every CTA folds
+  // all partials in CTA order itself -- the same operations in the same order in every
+  // CTA, so all hold the same scalars -- and solves the scalar recursion of layer lg
+  // (if lg > 0).  The two ratios of the closed form that do not depend on this phase's
+  // sums are formed while waiting.  ks: sweep of the layer finalised in this phase (its
+  // step goes into s_step).
   auto sync_phase = [&](T sA, T sB, T sa, T sb, float md, int lg, int ks) {
     const int buf = gphase & 1;
     double* part = a.partials + (size_t)buf * kPW * G;  // [word][CTA]
@@ -209,83 +209,69 @@ __global__ void __launch_bounds__(kThreads, 1) k_persist(PersistArgs a) {
         // this thread writes the CTA's partials, so its release covers them
 #pragma unroll
         for (int w = 0; w < 5; w++) part[(size_t)w * G + blockIdx.x] = v[w];
-        const unsigned old = atom_add_acq_rel(&sc->bar_count, 1u);
-        s_last = old == G * (unsigned)(gphase + 1) - 1u;
+        red_add_release(&sc->bar_count, 1u);
+        if (lg > 0) {
+          s_alpha = 1.0 / s_lam[lg - 1];
+          s_beta = s_lam[lg] / s_mu[lg + 1];
+        }
+        const unsigned target = G * (unsigned)(gphase + 1);
+        unsigned it = 0;
+        while ((int)(ld_relaxed_u32(&sc->bar_count) - target) < 0) {
+          if (*(volatile int*)&sc->flags & 6) break;  // an earlier wait gave up: do not wait again
+          if (++it > kSpinLimit) {
+            atomicOr(&sc->flags, 2);
+            break;
+          }
+        }
+        fence_acq_rel_gpu();
       }
     }
     __syncthreads();
-    if (s_last) {
-      // fold every CTA's partials in CTA order: warp w < 5 takes word w
-      if (wid < 5) {
-        double v = 0.0;
-        for (unsigned b = lane; b < G; b += 32) {
-          const double x = __ldcg(part + (size_t)wid * G + b);
-          v = (wid == 4) ? fmax(v, x) : v + x;
-        }
-        for (int m = 16; m > 0; m >>= 1) {
-          const double o = __shfl_xor_sync(0xffffffffu, v, m);
-          v = (wid == 4) ? fmax(v, o) : v + o;
-        }
-        if (lane == 0) s_red[wid][0] = v;
+    // fold every CTA's partials in CTA order: warp w < 5 takes word w
+    if (wid < 5) {
+      double v = 0.0;
+      for (unsigned b = lane; b < G; b += 32) {
+        const double x = __ldcg(part + (size_t)wid * G + b);
+        v = (wid == 4) ? fmax(v, x) : v + x;
       }
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        double f[5];
+      for (int m = 16; m > 0; m >>= 1) {
+        const double o = __shfl_xor_sync(0xffffffffu, v, m);
+        v = (wid == 4) ? fmax(v, o) : v + o;
+      }
+      if (lane == 0) s_red[wid][0] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double f[5];
 #pragma unroll
-        for (int w = 0; w < 5; w++) f[w] = s_red[w][0];
-        double* pub = sc->pub[buf];
-        if (kIR && lg > 0) {
-          // the correction sums plus the base's: the sums of the full (A, B) of layer lg
+      for (int w = 0; w < 5; w++) f[w] = s_red[w][0];
+      if (kIR && lg > 0) {
+        // the correction sums plus the base's: the sums of the full (A, B) of layer lg
 #pragma unroll
-          for (int w = 0; w < 4; w++) f[w] += sc->ir_sum[w][lg];
+        for (int w = 0; w < 4; w++) f[w] += sc->ir_sum[w][lg];
+      }
+      if (lg > 0) {
+        // closed-form limit of the inner loop (Eq. 12 and 14), then Eq. (13)
+        const double alpha = s_alpha, beta = s_beta;
+        const double aa = alpha * f[0], bb = beta * f[1];
+        const double mustar = bb / (1.0 - aa);
+        const double c1 = alpha * mustar;
+        s_c1 = V::from_d(c1);
+        s_c2 = V::from_d(beta);
+        if (kIR) {
+          s_d1 = V::from_d(c1 - sc->ir_c1[lg]);
+          s_d2 = V::from_d(beta - sc->ir_c2[lg]);
         }
-        if (lg > 0) {
-          // closed-form limit of the inner loop (Eq. 12 and 14), then Eq. (13)
-          const double alpha = 1.0 / s_lam[lg - 1];
-          const double beta = s_lam[lg] / s_mu[lg + 1];
-          const double aa = alpha * f[0], bb = beta * f[1];
-          const double mustar = bb / (1.0 - aa);
-          const double c1 = alpha * mustar;
-          pub[0] = c1;
-          pub[1] = beta;
-          pub[2] = a.lam * (c1 * f[2] + beta * f[3]);
-          pub[3] = mustar;
-          pub[5] = c1 - sc->ir_c1[lg];
-          pub[6] = beta - sc->ir_c2[lg];
+        s_lam[lg] = a.lam * (c1 * f[2] + beta * f[3]);
+        s_mu[lg] = mustar;
+        if (blockIdx.x == 0) {
           sc->c1[lg] = c1;
           sc->c2[lg] = beta;
           if (!isfinite(mustar) || !(aa < 1.0)) atomicOr(&sc->flags, 1);
         }
-        pub[4] = f[4];
-        if (gphase < 64) sc->t_phase[gphase] = globaltimer_ns();
-        red_add_release(&sc->bar_gen, 1u);
       }
-    } else if (threadIdx.x == 0) {
-      const unsigned target = s_gen0 + (unsigned)gphase + 1u;
-      unsigned it = 0;
-      while ((int)(ld_relaxed_u32(&sc->bar_gen) - target) < 0) {
-        if (*(volatile int*)&sc->flags & 6) break;  // an earlier wait gave up: do not wait again
-        if (++it > kSpinLimit) {
-          atomicOr(&sc->flags, 2);
-          break;
-        }
-      }
-      fence_acq_rel_gpu();
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      const double* pub = sc->pub[buf];
-      if (lg > 0) {
-        s_c1 = V::from_d(__ldcg(pub + 0));
-        s_c2 = V::from_d(__ldcg(pub + 1));
-        if (kIR) {
-          s_d1 = V::from_d(__ldcg(pub + 5));
-          s_d2 = V::from_d(__ldcg(pub + 6));
-        }
-        s_lam[lg] = __ldcg(pub + 2);
-        s_mu[lg] = __ldcg(pub + 3);
-      }
-      s_step[ks & 1] = fmax(s_step[ks & 1], __ldcg(pub + 4));
+      s_step[ks & 1] = fmax(s_step[ks & 1], f[4]);
+      if (blockIdx.x == 0 && gphase < 64) sc->t_phase[gphase] = globaltimer_ns();
     }
     __syncthreads();
     gphase++;
@@ -452,6 +438,7 @@ PrecBufs& hq_bufs(hq_solver* h, int prec) {
 
 int hq_run_sweeps(hq_solver* h, int prec, int nsweeps, cudaEvent_t ev0, cudaEvent_t ev1) {
   if (h->N < 2 || nsweeps < 1) return HQ_OK;
+  h->it_version++;
   // the barrier's arrival count (grid size x phases of a launch) stays below 2^31
   const int64_t per = ((int64_t)1 << 31) / ((int64_t)152 * 8 * (h->N - 1) + 1) - 1;
   const int cap = per > (1 << 20) ? (1 << 20) : (per < 1 ? 1 : (int)per);

@@ -436,6 +436,7 @@ int hq_compute_residual(hq_solver* h, double* residual_out) {
   if (rc != HQ_OK) return rc;
   rc = residual_pass(h);
   if (rc != HQ_OK) return rc;
+  h->res_version = h->it_version;
   double r = 0.0;
   HQ_CUDA(cudaMemcpyAsync(&r, h->summary + 3, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   HQ_CUDA(cudaStreamSynchronize(h->stream));
@@ -445,10 +446,16 @@ int hq_compute_residual(hq_solver* h, double* residual_out) {
 
 int hq_finalize(hq_solver* h, int prec, bool full_outputs, double* residual_out) {
   (void)prec;
-  int rc = prepare_fp64(h);
-  if (rc != HQ_OK) return rc;
-  rc = residual_pass(h);
-  if (rc != HQ_OK) return rc;
+  int rc = HQ_OK;
+  // a residual check of this very iterate already left the FP64 iterate, the layer law
+  // and the residual in place
+  if (h->res_version != h->it_version) {
+    rc = prepare_fp64(h);
+    if (rc != HQ_OK) return rc;
+    rc = residual_pass(h);
+    if (rc != HQ_OK) return rc;
+    h->res_version = h->it_version;
+  }
   if (full_outputs) {
     ScatterArgs sa;
     sa.N = h->N;

@@ -213,6 +213,7 @@ int hq_ir_assemble(hq_solver* h) {
 
 int hq_ir_begin(hq_solver* h, int from) {
   const int64_t Sp = h->Sp;
+  h->it_version++;
   const unsigned grid = (unsigned)((Sp + 255) / 256);
   if (from == HQ_PREC_IRC) {
     k_ir_rebase<<<grid, 256, 0, h->stream>>>(Sp, h->ir_base, (const float*)h->b32.p);

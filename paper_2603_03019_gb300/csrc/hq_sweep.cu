@@ -66,6 +66,7 @@ static int init_typed(hq_solver* h, const double* warm_dev) {
 
 int hq_init_iterate(hq_solver* h, int prec, const double* warm_y, int warm_mem) {
   const double* warm_dev = nullptr;
+  h->it_version++;
   if (warm_y) {
     if (warm_mem == HQ_HOST) {
       // stage through the y-order result buffer
@@ -106,6 +107,7 @@ __global__ void k_f32_to_df(int64_t S, const float* src, float2* dst) {
 
 int hq_convert_iterate(hq_solver* h, int from, int to) {
   if (from == to) return HQ_OK;
+  h->it_version++;
   if (to == HQ_PREC_IRC) return hq_ir_begin(h, from);
   if (from == HQ_PREC_IRC) {
     // the refinement's iterate is p0 + e: assemble it in FP64 first
