@@ -303,7 +303,7 @@ int hq_convert_tables(hq_solver* h);  // at hq_load: FP32 and DF64 copies of the
 
 // table (hq_table.cu)
 int hq_build_table(hq_solver* h);
-int hq_zeta_subset(hq_solver* h, double* buf, int bits, int count, bool superset);
+int hq_zeta_subset(hq_solver* h, long long* buf, int bits, int count, bool superset);  // 64-bit fixed point
 
 // sweep (hq_sweep.cu)
 int hq_init_iterate(hq_solver* h, int prec, const double* warm_y, int warm_mem);

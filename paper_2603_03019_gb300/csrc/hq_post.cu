@@ -308,15 +308,17 @@ __global__ void k_rho_final(int N, int nblk, const double* partials, const doubl
   rho[i] = t + summary[5];  // queued states: every unit busy
 }
 
-// h_i[X] = P{B} for B = X with a 0 inserted at bit i (unit i idle)
-__global__ void k_fill_idle(int N, const double* P, double* zeta) {
+// h_i[X] = P{B} for B = X with a 0 inserted at bit i (unit i idle), in 64-bit fixed
+// point P 2^61 (P <= 1 and every superset sum <= 1, so the sums are exact integer adds;
+// the quantum 2^-62 is far below the outputs' accuracy)
+__global__ void k_fill_idle(int N, const double* P, long long* zeta) {
   int64_t half = (int64_t)1 << (N - 1);
   int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= half * N) return;
   int i = (int)(g / half);
   int64_t X = g % half;
   int64_t y = (X & ((1ll << i) - 1)) | ((X >> i) << (i + 1));
-  zeta[g] = P[y];
+  zeta[g] = llrint(ldexp(P[y], 61));
 }
 
 __device__ __forceinline__ uint32_t squeeze_bit_p(uint32_t x, int u) {
@@ -325,13 +327,13 @@ __device__ __forceinline__ uint32_t squeeze_bit_p(uint32_t x, int u) {
 
 // R[j*N+i] = sum over states with unit i idle and every unit node j prefers to i
 // busy (the superset sum at pre_j(i)), plus waiting calls served by i
-__global__ void k_response(int N, int J, int mode, const uint32_t* pre, const double* zeta,
+__global__ void k_response(int N, int J, int mode, const uint32_t* pre, const long long* zeta,
                            const double* nu, double nu_sum, const double* summary, double* R) {
   int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= (int64_t)J * N) return;
   int i = (int)(g % N);
   int64_t half = (int64_t)1 << (N - 1);
-  double v = zeta[(int64_t)i * half + squeeze_bit_p(pre[g], i)];
+  double v = ldexp((double)zeta[(int64_t)i * half + squeeze_bit_p(pre[g], i)], -61);
   if (mode != HQ_LOSS) v += summary[2] * nu[i] / nu_sum;
   R[g] = v;
 }
@@ -473,17 +475,19 @@ int hq_finalize(hq_solver* h, int prec, bool full_outputs, double* residual_out)
     HQ_LAUNCHED();
     if (h->N >= 2) {
       int64_t half = (int64_t)1 << (h->N - 1);
-      k_fill_idle<<<(unsigned)((half * h->N + 255) / 256), 256, 0, h->stream>>>(h->N, h->P, h->zeta);
+      k_fill_idle<<<(unsigned)((half * h->N + 255) / 256), 256, 0, h->stream>>>(h->N, h->P,
+                                                                               (long long*)h->zeta);
       HQ_LAUNCHED();
-      rc = hq_zeta_subset(h, h->zeta, h->N - 1, h->N, true);
+      rc = hq_zeta_subset(h, (long long*)h->zeta, h->N - 1, h->N, true);
       if (rc != HQ_OK) return rc;
     } else {
       // one unit: the only idle state is B = 0
-      HQ_CUDA(cudaMemcpyAsync(h->zeta, h->P, sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+      k_fill_idle<<<1, 32, 0, h->stream>>>(1, h->P, (long long*)h->zeta);
+      HQ_LAUNCHED();
     }
     int64_t jn = (int64_t)h->J * h->N;
     k_response<<<(unsigned)((jn + 255) / 256), 256, 0, h->stream>>>(
-        h->N, h->J, h->mode, h->pre, h->zeta, h->nu, h->nu_sum, h->summary, h->R);
+        h->N, h->J, h->mode, h->pre, (const long long*)h->zeta, h->nu, h->nu_sum, h->summary, h->R);
     HQ_LAUNCHED();
     k_workload<<<(unsigned)((jn + 255) / 256), 256, 0, h->stream>>>(h->N, h->J, h->lam_j, h->nu,
                                                                   h->R, h->W);

@@ -11,8 +11,11 @@
 // the rate is the subset sum F_u(X) = sum_{S subset of X} g_u(S) at X = m - u.  So the
 // whole table is N histograms plus N subset-sum (zeta) transforms over N-1 bits:
 // O(N^2 2^N) work independent of J, instead of one first-idle search per
-// (state, node) pair.  Sums are FP64; the emit writes FP64, double-float and FP32
-// copies in the pull layout
+// (state, node) pair.  The sums are exact: each lambda_j is quantised once to 64-bit
+// fixed point (a power-of-two scale that keeps lambda = sum_j lambda_j below 2^61,
+// so the quantum is ~2^-62 lambda) and every sum after that is an integer add, which
+// also keeps the transform off GB300's slow FP64 pipe.  The emit converts to FP64 in
+// the pull layout (FP32 and double-float copies follow from it)
 //     T[toff(n) + s C(N,n) + k] = F_{c_s}(m_k - c_s),
 // m_k the rank-k state of layer n and c_s its s-th busy unit, so the sweep reads
 // slot s of consecutive states contiguously.
@@ -37,22 +40,22 @@ __global__ void k_prefix_masks(int N, int J, const int32_t* pref, uint32_t* pre)
 }
 
 // g_u histogram: one CTA per unit u.  Each node j whose key is new (no lower
-// j' shares it) sums lambda over all nodes with that key in increasing j, so the
+// j' shares it) sums its group's rates, quantised as llrint(lambda_j 2^e), so the
 // result does not depend on thread timing.
-__global__ void k_histogram(int N, int J, const uint32_t* pre, const double* lam_j,
-                            double* zeta) {
+__global__ void k_histogram(int N, int J, const uint32_t* pre, const double* lam_j, int e,
+                            long long* zeta) {
   int u = blockIdx.x;
   int64_t half = (int64_t)1 << (N - 1);
-  double* F = zeta + (int64_t)u * half;
+  long long* F = zeta + (int64_t)u * half;
   for (int j = threadIdx.x; j < J; j += blockDim.x) {
     uint32_t key = squeeze_bit(__ldg(pre + (int64_t)j * N + u), u);
     bool leader = true;
     for (int jp = 0; jp < j && leader; jp++)
       if (squeeze_bit(__ldg(pre + (int64_t)jp * N + u), u) == key) leader = false;
     if (!leader) continue;
-    double s = 0.0;
+    long long s = 0;
     for (int jp = j; jp < J; jp++)
-      if (squeeze_bit(__ldg(pre + (int64_t)jp * N + u), u) == key) s += __ldg(lam_j + jp);
+      if (squeeze_bit(__ldg(pre + (int64_t)jp * N + u), u) == key) s += llrint(ldexp(__ldg(lam_j + jp), e));
     F[key] = s;
   }
 }
@@ -60,19 +63,20 @@ __global__ void k_histogram(int N, int J, const uint32_t* pre, const double* lam
 // ---------------------------------------------------------------------------
 // subset-sum (zeta) transform F(X) = sum_{S subset X} f(S), or the superset
 // version F(X) = sum_{S superset X} f(S), over `bits` bits for `count` arrays
-// laid end to end.  Pass 1 handles the low bits inside a shared-memory tile of
-// contiguous elements; later passes handle groups of high bits with tiles made
-// of 2^g strided rows of kCols contiguous elements.
+// laid end to end, of 64-bit fixed-point values (exact integer adds).  Pass 1
+// handles the low bits inside a shared-memory tile of contiguous elements; later
+// passes handle groups of high bits with tiles made of 2^g strided rows of kCols
+// contiguous elements.
 // ---------------------------------------------------------------------------
 constexpr int kTileLog = 12;           // 4096 doubles = 32 KB
 constexpr int kColsLog = 4;            // 16 contiguous doubles per row in later passes
 
-__global__ void k_zeta_low(double* buf, int bits, int tile_log, int64_t ntiles, bool superset) {
-  extern __shared__ double t[];
+__global__ void k_zeta_low(long long* buf, int bits, int tile_log, int64_t ntiles, bool superset) {
+  extern __shared__ long long t[];
   int64_t tile = blockIdx.x;
   if (tile >= ntiles) return;
   int64_t tsize = (int64_t)1 << tile_log;
-  double* base = buf + tile * tsize;
+  long long* base = buf + tile * tsize;
   for (int64_t i = threadIdx.x; i < tsize; i += blockDim.x) t[i] = base[i];
   __syncthreads();
   int nb = bits < tile_log ? bits : tile_log;
@@ -90,9 +94,9 @@ __global__ void k_zeta_low(double* buf, int bits, int tile_log, int64_t ntiles, 
 }
 
 // bits [b0, b0+g) of each array; tile = 2^g rows (stride 2^b0) x 2^cols_log columns
-__global__ void k_zeta_high(double* buf, int bits, int b0, int g, int cols_log, int64_t per_array,
+__global__ void k_zeta_high(long long* buf, int bits, int b0, int g, int cols_log, int64_t per_array,
                             int64_t tiles_per_array, int count, bool superset) {
-  extern __shared__ double t[];
+  extern __shared__ long long t[];
   int64_t tid = blockIdx.x;
   int a = (int)(tid / tiles_per_array);
   if (a >= count) return;
@@ -101,7 +105,7 @@ __global__ void k_zeta_high(double* buf, int bits, int b0, int g, int cols_log, 
   int64_t colblocks = ((int64_t)1 << b0) >> cols_log;
   int64_t cb = tix % colblocks;
   int64_t above = tix / colblocks;
-  double* arr = buf + (int64_t)a * per_array;
+  long long* arr = buf + (int64_t)a * per_array;
   int64_t start = (above << (b0 + g)) + (cb << cols_log);
   int rows = 1 << g, cols = 1 << cols_log;
   int64_t stride = (int64_t)1 << b0;
@@ -129,12 +133,12 @@ __global__ void k_zeta_high(double* buf, int bits, int b0, int g, int cols_log, 
   (void)bits;
 }
 
-int hq_zeta_subset(hq_solver* h, double* buf, int bits, int count, bool superset) {
+int hq_zeta_subset(hq_solver* h, long long* buf, int bits, int count, bool superset) {
   if (bits <= 0) return HQ_OK;
   int64_t per = (int64_t)1 << bits;
   int tl = bits < kTileLog ? bits : kTileLog;
   int64_t ntiles = (per >> tl) * count;
-  size_t smem = sizeof(double) << tl;
+  size_t smem = sizeof(long long) << tl;
   HQ_CUDA(cudaFuncSetAttribute(k_zeta_low, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024));
   HQ_CUDA(cudaFuncSetAttribute(k_zeta_high, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024));
   k_zeta_low<<<(unsigned)ntiles, 256, smem, h->stream>>>(buf, bits, tl, ntiles, superset);
@@ -148,7 +152,7 @@ int hq_zeta_subset(hq_solver* h, double* buf, int bits, int count, bool superset
     int64_t colblocks = ((int64_t)1 << b0) >> cols_log;
     int64_t above = per >> (b0 + g);
     int64_t tpa = colblocks * above;
-    size_t sm = sizeof(double) << (g + cols_log);
+    size_t sm = sizeof(long long) << (g + cols_log);
     k_zeta_high<<<(unsigned)(tpa * count), 256, sm, h->stream>>>(buf, bits, b0, g, cols_log, per,
                                                                 tpa, count, superset);
     HQ_LAUNCHED();
@@ -165,8 +169,8 @@ struct EmitArgs {
   int64_t lpad[HQ_MAXN + 1];  // row stride
 };
 
-// one thread per state of layers 1..N: slot s <- F_{c_s}(m - c_s)
-__global__ void k_emit(EmitArgs a, int64_t S, const uint32_t* masks, const double* zeta,
+// one thread per state of layers 1..N: slot s <- F_{c_s}(m - c_s) 2^-e
+__global__ void k_emit(EmitArgs a, int64_t S, const uint32_t* masks, const long long* zeta, int e,
                        double* T64) {
   int64_t g = a.off[1] + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= S) return;
@@ -180,7 +184,7 @@ __global__ void k_emit(EmitArgs a, int64_t S, const uint32_t* masks, const doubl
   int s = 0;
   for (uint32_t y = x; y; y &= y - 1, s++) {
     int u = __ffs(y) - 1;
-    T64[a.toff[n] + (int64_t)s * Ln + k] = __ldg(zeta + (int64_t)u * half + squeeze_bit(x, u));
+    T64[a.toff[n] + (int64_t)s * Ln + k] = ldexp((double)__ldg(zeta + (int64_t)u * half + squeeze_bit(x, u)), -e);
   }
 }
 
@@ -189,10 +193,15 @@ int hq_build_table(hq_solver* h) {
   int64_t half = (int64_t)1 << (N - 1);
   k_prefix_masks<<<(J + 255) / 256, 256, 0, h->stream>>>(N, J, h->pref, h->pre);
   HQ_LAUNCHED();
-  HQ_CUDA(cudaMemsetAsync(h->zeta, 0, sizeof(double) * half * N, h->stream));
-  k_histogram<<<N, 256, 0, h->stream>>>(N, J, h->pre, h->lam_j, h->zeta);
+  // the fixed-point scale 2^e keeps every sum (at most lambda) below 2^61
+  int ex = 0;
+  frexp(h->lam > 0.0 ? h->lam : 1.0, &ex);  // lambda < 2^ex
+  const int e = 61 - ex;
+  long long* z = (long long*)h->zeta;
+  HQ_CUDA(cudaMemsetAsync(z, 0, sizeof(long long) * half * N, h->stream));
+  k_histogram<<<N, 256, 0, h->stream>>>(N, J, h->pre, h->lam_j, e, z);
   HQ_LAUNCHED();
-  int rc = hq_zeta_subset(h, h->zeta, N - 1, N, false);
+  int rc = hq_zeta_subset(h, z, N - 1, N, false);
   if (rc != HQ_OK) return rc;
   EmitArgs a;
   a.N = N;
@@ -206,7 +215,7 @@ int hq_build_table(hq_solver* h) {
   }
   int64_t cnt = h->Sp - h->off[1];
   k_emit<<<(unsigned)((cnt + 255) / 256), 256, 0, h->stream>>>(
-      a, h->Sp, h->masks, h->zeta, (double*)h->b64.T);
+      a, h->Sp, h->masks, z, e, (double*)h->b64.T);
   HQ_LAUNCHED();
   return HQ_OK;
 }
