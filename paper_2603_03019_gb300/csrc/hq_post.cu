@@ -318,7 +318,7 @@ __global__ void k_fill_idle(int N, const double* P, long long* zeta) {
   int i = (int)(g / half);
   int64_t X = g % half;
   int64_t y = (X & ((1ll << i) - 1)) | ((X >> i) << (i + 1));
-  zeta[g] = llrint(ldexp(P[y], 61));
+  zeta[g] = __double2ll_rn(P[y] * 0x1p61);
 }
 
 __device__ __forceinline__ uint32_t squeeze_bit_p(uint32_t x, int u) {
@@ -333,7 +333,7 @@ __global__ void k_response(int N, int J, int mode, const uint32_t* pre, const lo
   if (g >= (int64_t)J * N) return;
   int i = (int)(g % N);
   int64_t half = (int64_t)1 << (N - 1);
-  double v = ldexp((double)zeta[(int64_t)i * half + squeeze_bit_p(pre[g], i)], -61);
+  double v = (double)zeta[(int64_t)i * half + squeeze_bit_p(pre[g], i)] * 0x1p-61;
   if (mode != HQ_LOSS) v += summary[2] * nu[i] / nu_sum;
   R[g] = v;
 }

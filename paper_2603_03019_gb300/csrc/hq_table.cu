@@ -40,9 +40,9 @@ __global__ void k_prefix_masks(int N, int J, const int32_t* pref, uint32_t* pre)
 }
 
 // g_u histogram: one CTA per unit u.  Each node j whose key is new (no lower
-// j' shares it) sums its group's rates, quantised as llrint(lambda_j 2^e), so the
-// result does not depend on thread timing.
-__global__ void k_histogram(int N, int J, const uint32_t* pre, const double* lam_j, int e,
+// j' shares it) sums its group's rates, each quantised as round(lambda_j scale) with
+// scale a power of two, so the result does not depend on thread timing.
+__global__ void k_histogram(int N, int J, const uint32_t* pre, const double* lam_j, double scale,
                             long long* zeta) {
   int u = blockIdx.x;
   int64_t half = (int64_t)1 << (N - 1);
@@ -55,7 +55,7 @@ __global__ void k_histogram(int N, int J, const uint32_t* pre, const double* lam
     if (!leader) continue;
     long long s = 0;
     for (int jp = j; jp < J; jp++)
-      if (squeeze_bit(__ldg(pre + (int64_t)jp * N + u), u) == key) s += llrint(ldexp(__ldg(lam_j + jp), e));
+      if (squeeze_bit(__ldg(pre + (int64_t)jp * N + u), u) == key) s += __double2ll_rn(__ldg(lam_j + jp) * scale);
     F[key] = s;
   }
 }
@@ -68,8 +68,9 @@ __global__ void k_histogram(int N, int J, const uint32_t* pre, const double* lam
 // passes handle groups of high bits with tiles made of 2^g strided rows of kCols
 // contiguous elements.
 // ---------------------------------------------------------------------------
-constexpr int kTileLog = 12;           // 4096 doubles = 32 KB
-constexpr int kColsLog = 4;            // 16 contiguous doubles per row in later passes
+constexpr int kTileLog = 14;           // 16384 elements = 128 KB of shared memory per tile
+constexpr int kColsLog = 5;            // 32 contiguous elements (256 B) per row in later passes
+constexpr int kZetaThreads = 1024;
 
 __global__ void k_zeta_low(long long* buf, int bits, int tile_log, int64_t ntiles, bool superset) {
   extern __shared__ long long t[];
@@ -139,9 +140,10 @@ int hq_zeta_subset(hq_solver* h, long long* buf, int bits, int count, bool super
   int tl = bits < kTileLog ? bits : kTileLog;
   int64_t ntiles = (per >> tl) * count;
   size_t smem = sizeof(long long) << tl;
-  HQ_CUDA(cudaFuncSetAttribute(k_zeta_low, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024));
-  HQ_CUDA(cudaFuncSetAttribute(k_zeta_high, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024));
-  k_zeta_low<<<(unsigned)ntiles, 256, smem, h->stream>>>(buf, bits, tl, ntiles, superset);
+  const int smax = (int)(sizeof(long long) << kTileLog);
+  HQ_CUDA(cudaFuncSetAttribute(k_zeta_low, cudaFuncAttributeMaxDynamicSharedMemorySize, smax));
+  HQ_CUDA(cudaFuncSetAttribute(k_zeta_high, cudaFuncAttributeMaxDynamicSharedMemorySize, smax));
+  k_zeta_low<<<(unsigned)ntiles, kZetaThreads, smem, h->stream>>>(buf, bits, tl, ntiles, superset);
   HQ_LAUNCHED();
   int b0 = tl;
   while (b0 < bits) {
@@ -153,7 +155,7 @@ int hq_zeta_subset(hq_solver* h, long long* buf, int bits, int count, bool super
     int64_t above = per >> (b0 + g);
     int64_t tpa = colblocks * above;
     size_t sm = sizeof(long long) << (g + cols_log);
-    k_zeta_high<<<(unsigned)(tpa * count), 256, sm, h->stream>>>(buf, bits, b0, g, cols_log, per,
+    k_zeta_high<<<(unsigned)(tpa * count), kZetaThreads, sm, h->stream>>>(buf, bits, b0, g, cols_log, per,
                                                                 tpa, count, superset);
     HQ_LAUNCHED();
     b0 += g;
@@ -169,8 +171,8 @@ struct EmitArgs {
   int64_t lpad[HQ_MAXN + 1];  // row stride
 };
 
-// one thread per state of layers 1..N: slot s <- F_{c_s}(m - c_s) 2^-e
-__global__ void k_emit(EmitArgs a, int64_t S, const uint32_t* masks, const long long* zeta, int e,
+// one thread per state of layers 1..N: slot s <- F_{c_s}(m - c_s) / scale
+__global__ void k_emit(EmitArgs a, int64_t S, const uint32_t* masks, const long long* zeta, double inv_scale,
                        double* T64) {
   int64_t g = a.off[1] + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= S) return;
@@ -184,7 +186,7 @@ __global__ void k_emit(EmitArgs a, int64_t S, const uint32_t* masks, const long 
   int s = 0;
   for (uint32_t y = x; y; y &= y - 1, s++) {
     int u = __ffs(y) - 1;
-    T64[a.toff[n] + (int64_t)s * Ln + k] = ldexp((double)__ldg(zeta + (int64_t)u * half + squeeze_bit(x, u)), -e);
+    T64[a.toff[n] + (int64_t)s * Ln + k] = (double)__ldg(zeta + (int64_t)u * half + squeeze_bit(x, u)) * inv_scale;
   }
 }
 
@@ -197,9 +199,10 @@ int hq_build_table(hq_solver* h) {
   int ex = 0;
   frexp(h->lam > 0.0 ? h->lam : 1.0, &ex);  // lambda < 2^ex
   const int e = 61 - ex;
+  const double scale = ldexp(1.0, e);  // exact powers of two: the scaling is exact
   long long* z = (long long*)h->zeta;
   HQ_CUDA(cudaMemsetAsync(z, 0, sizeof(long long) * half * N, h->stream));
-  k_histogram<<<N, 256, 0, h->stream>>>(N, J, h->pre, h->lam_j, e, z);
+  k_histogram<<<N, 256, 0, h->stream>>>(N, J, h->pre, h->lam_j, scale, z);
   HQ_LAUNCHED();
   int rc = hq_zeta_subset(h, z, N - 1, N, false);
   if (rc != HQ_OK) return rc;
@@ -215,7 +218,7 @@ int hq_build_table(hq_solver* h) {
   }
   int64_t cnt = h->Sp - h->off[1];
   k_emit<<<(unsigned)((cnt + 255) / 256), 256, 0, h->stream>>>(
-      a, h->Sp, h->masks, z, e, (double*)h->b64.T);
+      a, h->Sp, h->masks, z, 1.0 / scale, (double*)h->b64.T);
   HQ_LAUNCHED();
   return HQ_OK;
 }
