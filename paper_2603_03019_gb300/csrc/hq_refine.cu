@@ -42,6 +42,7 @@ struct IrArgs {
   const uint32_t* RL;
   const uint32_t* RH;
   const double* T;   // FP64 pull-form table
+  const float* T32;  // FP32 pull-form table
   const double* r;   // FP64 r_m
   const double* nu;  // FP64 nu_i
   const double* pb;  // the base p0
@@ -90,7 +91,9 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 // kPass 0: the base terms of every state of layers 1..N-1 from p0 (FP64), and per-item
 // partial sums {sum mu_m A0_m, sum mu_m B0_m, sum A0_m, sum B0_m} (mu_m r_m = 1 - lambda r_m).
 // kPass 1: G_rho, G_A, G_B of every state of layers 2..N-1 from the stored base terms
-// of layer n-1 (zero in layer 1, which pulls from the empty state).
+// of layer n-1 (zero in layer 1, which pulls from the empty state), in FP32: G_rho is
+// of the correction's size and G_A, G_B only ever multiply d1, d2, so FP32 rounding
+// of them is rounding relative to the correction.
 template <int kPass>
 __global__ void __launch_bounds__(256) k_ir_pass(IrArgs a) {
   const int lane = threadIdx.x & 31;
@@ -143,23 +146,24 @@ __global__ void __launch_bounds__(256) k_ir_pass(IrArgs a) {
         q[3] = v3;
       }
     } else {
-      double gR = 0.0, gA = 0.0, gB = 0.0;
+      float gR = 0.f, gA = 0.f, gB = 0.f;
       if (n > 1) {
         const float* bd = a.ir + a.off[n - 1];
+        const float* t32 = a.T32 + a.toff[n] + kq;
         visit(
             a, d, x, w0, w1, w2,
             [&](int s, uint32_t rk) {
-              const double t = tcol[s * lp];
-              gR = fma(t, (double)bd[rk], gR);
-              gA = fma(t, (double)bd[Sp + rk], gA);
-              gB = fma(t, (double)bd[2 * Sp + rk], gB);
+              const float t = __ldg(t32 + s * lp);
+              gR = fmaf(t, bd[rk], gR);
+              gA = fmaf(t, bd[Sp + rk], gA);
+              gB = fmaf(t, bd[2 * Sp + rk], gB);
             },
             [&](int, uint32_t) {});
       }
       if (act) {
-        a.ir[3 * Sp + gi] = (float)gR;
-        a.ir[4 * Sp + gi] = (float)gA;
-        a.ir[5 * Sp + gi] = (float)gB;
+        a.ir[3 * Sp + gi] = gR;
+        a.ir[4 * Sp + gi] = gA;
+        a.ir[5 * Sp + gi] = gB;
       }
     }
   }
@@ -245,6 +249,7 @@ int hq_ir_begin(hq_solver* h, int from) {
     a.RL = h->RL;
     a.RH = h->RH;
     a.T = (const double*)h->b64.T;
+    a.T32 = (const float*)h->b32.T;
     a.r = (const double*)h->b64.r;
     a.nu = h->nu;
     a.pb = h->ir_base;
