@@ -52,9 +52,9 @@ WORKLOADS = {
 # layer scalars, the birth-death step and the residual)
 DTYPE = {"fp32+ir": "f32 sweeps + f64 refinement base", "fp32+df64": "f32 + df64 sweeps",
          "fp32+fp64": "f32 + f64 sweeps", "fp64": "f64", "df64": "df64", "fp32": "f32"}
-SWEEP_DRAM_PER_ALG_BYTE = 298.587e6 / 251658120
+SWEEP_DRAM_PER_ALG_BYTE = 298.461e6 / 251658120
 TRAFFIC_SOURCE = ("ncu --set full of one FP32 sweep at N=22 (profiles/k_persist_fp32_n22_set_full.md): "
-                  "298.6 MB DRAM for 251.7 MB algorithmic, scaled by algorithmic bytes")
+                  "298.5 MB DRAM for 251.7 MB algorithmic, scaled by algorithmic bytes")
 METRIC = ("state-updates/s (solve to 1e-10 relative balance residual; N=24 time-to-tol, "
           "FP32+refinement vs plain FP64, reported beside it)")
 BASE_SEED = {"n24": 3001, "n23": 3001, "n22": 3001, "n20": 2001, "n10": 1001}

@@ -87,7 +87,9 @@ typedef struct hq_opts {
   int warm_mem;        /* hq_mem of warm_p */
   const double* warm_p;/* HQ_WARM_GIVEN: start vector p_n(B) in y-order, length 2^N */
   double fp32_stall;   /* mixed modes: leave FP32 when the step's decay per check is
-                          worse than this ratio (0 = default 0.9); HQ_PREC_FP32_IR
+                          worse than this ratio (0 = default: 0.75 for HQ_PREC_FP32_IR,
+                          whose correction sweeps cost about an FP32 sweep, 0.9 for
+                          DF64 / FP64 refinement); HQ_PREC_FP32_IR
                           also re-bases when four checks in a row decay worse than it,
                           or one does after the correction shrank by 1e4 */
   double omega;        /* over-relaxation of the outer iteration (not in the paper):

@@ -284,7 +284,10 @@ extern "C" int hq_solve(hq_solver* h, const hq_opts* opts_in, hq_stats* stats) {
   if (o.tol_kind != HQ_TOL_STEP && o.tol_kind != HQ_TOL_RESIDUAL) { hq_set_error("bad tol_kind"); return HQ_EINVAL; }
   if (o.warm_start == HQ_WARM_GIVEN && !o.warm_p) { hq_set_error("warm_p is NULL"); return HQ_EINVAL; }
   if (o.warm_start == HQ_WARM_MLP && !h->mlp) { hq_set_error("no warm-start model is attached"); return HQ_EINVAL; }
-  double stall = o.fp32_stall > 0.0 ? o.fp32_stall : 0.9;
+  // FP32 sweeps stall at their rounding floor; leaving them a check early costs little
+  // when the refinement's sweeps cost about as much (correction sweeps), a check late
+  // wastes eight sweeps
+  double stall = o.fp32_stall > 0.0 ? o.fp32_stall : (o.precision == HQ_PREC_FP32_IR ? 0.75 : 0.9);
   if (!(o.omega < 2.0) || (o.omega >= 0.0 && o.omega < 1.0 && o.omega != 0.0)) {
     hq_set_error("omega must be 0, in [1, 2), or negative (automatic)");
     return HQ_EINVAL;
@@ -306,6 +309,8 @@ extern "C" int hq_solve(hq_solver* h, const hq_opts* opts_in, hq_stats* stats) {
   }
   int rebases = 0, ir_bases = 0, ir_flat = 0;
   double step_base = 0.0;  // the first step of the current refinement base
+  double last_ratio = 0.0;  // the step decay of the check before
+  int phase_checks = 0;     // checks since the last change of precision or base
   int ph = 0;
   int sweeps[2] = {0, 0};
   int total = 0, checks = 0, res_checks = 0, since_res = 0, stalled = 0;
@@ -369,6 +374,17 @@ extern "C" int hq_solve(hq_solver* h, const hq_opts* opts_in, hq_stats* stats) {
       break;
     }
     const double ratio = prev_check_step > 0.0 ? step / prev_check_step : 0.0;
+    const bool last_phase = ph == nph - 1;
+    phase_checks++;
+    // leave FP32 once its steps stop shrinking geometrically (rounding floor); correction
+    // sweeps cost about what FP32 sweeps cost, so refinement by them also starts when
+    // the decay turns abruptly worse than the check before (past the start's transient)
+    const bool leave =
+        !last_phase &&
+        (step == 0.0 ||
+         (prev_check_step > 0.0 &&
+          (ratio > stall || (phases[ph + 1] == HQ_PREC_IRC && checks > 4 && last_ratio > 0.0 &&
+                             ratio > 0.5 && ratio > 1.5 * last_ratio))));
     if (auto_omega) {
       // Young's optimal relaxation for the observed contraction: with Algorithm 1's
       // per-sweep rate r (measured over the third check, past the start's transient),
@@ -379,22 +395,26 @@ extern "C" int hq_solve(hq_solver* h, const hq_opts* opts_in, hq_stats* stats) {
         const double r = pow(ratio, 1.0 / nrun);
         const double wopt = 2.0 / (1.0 + sqrt(1.0 - r));
         h->omega = fmin(1.0 + 0.9 * (wopt - 1.0), 1.5);
-      } else if (h->omega > 1.0 && ratio >= 1.0) {
+      } else if (h->omega > 1.0 && ratio >= 1.0 && !leave && phase_checks > 3) {
+        // (a check that ends the FP32 phase stalls on rounding, not on omega, and the
+        // first three checks after a change of precision or base clear the old
+        // rounding, which can grow the steps before they fall)
         h->omega = 1.0 + 0.5 * (h->omega - 1.0);
       }
     }
-    const bool last_phase = ph == nph - 1;
     if (!last_phase) {
-      // leave FP32 once its steps stop shrinking geometrically (rounding floor)
-      if ((prev_check_step > 0.0 && ratio > stall) || step == 0.0) {
+      if (leave) {
         rc = hq_convert_iterate(h, phases[ph], phases[ph + 1]);
         if (rc != HQ_OK) return rc;
         if (phases[ph + 1] == HQ_PREC_IRC) ir_bases++;
         ph++;
         prev_check_step = 0.0;
+        last_ratio = 0.0;
+        phase_checks = 0;
         continue;
       }
       prev_check_step = step;
+      last_ratio = ratio;
       continue;
     }
     if (o.tol_kind == HQ_TOL_STEP) {
@@ -432,6 +452,8 @@ extern "C" int hq_solve(hq_solver* h, const hq_opts* opts_in, hq_stats* stats) {
         ir_flat = 0;
         step_base = 0.0;
         prev_check_step = 0.0;
+        last_ratio = 0.0;
+        phase_checks = 0;
         stalled = 0;
         continue;
       }
@@ -443,6 +465,7 @@ extern "C" int hq_solve(hq_solver* h, const hq_opts* opts_in, hq_stats* stats) {
       stalled = 0;
     }
     prev_check_step = step;
+    last_ratio = ratio;
   }
   if (status == HQ_EDIVERGED || status == HQ_ETIMEOUT) {
     if (stats) {

@@ -171,6 +171,8 @@ struct DevScalars {
   double red[16];              // results of whole-vector reductions
   double lsum[HQ_MAXN + 1];    // sum_m p_n(B_m) per layer (whole-vector pass)
   double lmu[HQ_MAXN + 1];     // sum_m mu_m p_n(B_m) per layer
+  long long lsum_q[HQ_MAXN + 1];  // the same two sums in 64-bit fixed point (exact adds)
+  long long lmu_q[HQ_MAXN + 1];
   double res_num[HQ_MAXN + 1]; // max_m |out_m - in_m| per layer (residual)
   double res_den[HQ_MAXN + 1]; // max_m out_m per layer
   double fac[HQ_MAXN + 1];     // P{B} = fac[w(B)] * p_w(B) after the birth-death step

@@ -1,5 +1,6 @@
 // From the conditional probabilities to the stationary distribution and the
-// performance measures, all in FP64:
+// performance measures, in FP64 (sums of many non-negative terms in exact 64-bit fixed
+// point):
 //   * layer totals S_n = sum_m p_n(B_m), M_n = sum_m mu_m p_n(B_m) (Eq. 6-7);
 //   * p(n) of the birth-death process -- Eq. (10), Proposition 2 (finite
 //     buffer) and the Remark (infinite buffer) -- by a log-scale recursion;
@@ -68,32 +69,72 @@ __device__ void fold_partials(const double* partials, bool a_max, bool b_max, do
   B = b;
 }
 
+// Layer totals S_n = sum_m p_n(B_m) and M_n = sum_m mu_m p_n(B_m) of every layer in one
+// pass, in 64-bit fixed point: p at 2^61 (p <= 1) and mu_m p at 2^em (sum nu < 2^(61-em)),
+// mu_m itself an exact integer sum of the quantised nu_i.  Integer adds are exact, so the
+// totals do not depend on the order in which warps add them: each warp takes a
+// contiguous run of 32-state chunks (layers start on 32-entry boundaries, so a chunk
+// lies in one layer) and adds its running sums to the layer's accumulators whenever
+// the layer changes.  k_layer_totals then converts them to FP64.
+struct LayerSumArgs {
+  int N;
+  int64_t off[HQ_MAXN + 2];
+  int64_t lsize[HQ_MAXN + 1];
+  double scale_nu;  // 2^em
+};
+
 template <class V>
-__global__ void k_layer_sum(int n, int64_t Ln, const uint32_t* masks, const typename V::T* p,
-                            const double* nu, double* partials, DevScalars* sc) {
-  __shared__ double s[64];
-  __shared__ bool s_last;
-  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  double v = 0.0, vm = 0.0;
-  if (k < Ln) {
-    v = V::to_d(p[k]);
-    uint32_t x = masks[k];
-    double mu = 0.0;
-    for (uint32_t y = x; y; y &= y - 1) mu += __ldg(nu + (__ffs(y) - 1));
-    vm = v * mu;
+__global__ void __launch_bounds__(256) k_layer_sum(LayerSumArgs a, const uint32_t* masks,
+                                                   const typename V::T* p, const double* nu,
+                                                   DevScalars* sc) {
+  __shared__ long long s_nu[HQ_MAXN];
+  if (threadIdx.x < a.N) s_nu[threadIdx.x] = __double2ll_rn(nu[threadIdx.x] * a.scale_nu);
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int64_t chunks = a.off[a.N + 1] >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t per = (chunks + nw - 1) / nw;
+  const int64_t c0 = gw * per, c1 = c0 + per < chunks ? c0 + per : chunks;
+  int n = 0;
+  long long sv = 0, sm = 0;
+  for (int64_t c = c0; c < c1; c++) {
+    const int64_t g = (c << 5) + lane;
+    int nc = n;
+    while (nc < a.N && a.off[nc + 1] <= (c << 5)) nc++;
+    if (nc != n) {
+      if (lane == 0 && (sv | sm)) {
+        atomicAdd((unsigned long long*)&sc->lsum_q[n], (unsigned long long)sv);
+        atomicAdd((unsigned long long*)&sc->lmu_q[n], (unsigned long long)sm);
+      }
+      sv = sm = 0;
+      n = nc;
+    }
+    long long v = 0, vm = 0;
+    if (g - a.off[n] < a.lsize[n]) {
+      const double pv = V::to_d(p[g]);
+      long long mq = 0;
+      for (uint32_t y = masks[g]; y; y &= y - 1) mq += s_nu[__ffs(y) - 1];
+      v = __double2ll_rn(pv * 0x1p61);
+      vm = __double2ll_rn(pv * (double)mq);  // (mu_m 2^em) p
+    }
+    for (int m = 16; m > 0; m >>= 1) {
+      v += __shfl_xor_sync(0xffffffffu, v, m);
+      vm += __shfl_xor_sync(0xffffffffu, vm, m);
+    }
+    sv += v;
+    sm += vm;
   }
-  block_reduce2(v, vm, false, false, s);
-  if (threadIdx.x == 0) {
-    partials[2 * (int64_t)blockIdx.x] = v;
-    partials[2 * (int64_t)blockIdx.x + 1] = vm;
+  if (lane == 0 && (sv | sm) && c0 < c1) {
+    atomicAdd((unsigned long long*)&sc->lsum_q[n], (unsigned long long)sv);
+    atomicAdd((unsigned long long*)&sc->lmu_q[n], (unsigned long long)sm);
   }
-  if (!arrive_last_post(&sc->ticket[2], &s_last)) return;
-  double A, B;
-  fold_partials(partials, false, false, s, A, B);
-  if (threadIdx.x == 0) {
-    sc->lsum[n] = A;
-    sc->lmu[n] = B;
-    sc->ticket[2] = 0u;
+}
+
+__global__ void k_layer_totals(int N, double inv_scale_nu, DevScalars* sc) {
+  for (int n = threadIdx.x; n <= N; n += blockDim.x) {
+    sc->lsum[n] = (double)sc->lsum_q[n] * 0x1p-61;
+    sc->lmu[n] = (double)sc->lmu_q[n] * inv_scale_nu;
   }
 }
 
@@ -265,22 +306,29 @@ __global__ void k_scatter(ScatterArgs a, int64_t S, const uint32_t* masks, const
 }
 
 // rho_i = sum_{B containing i} P{B}: warp w covers 32 consecutive y; bits 0..4 of
-// y vary across the lanes (masked warp sums), higher bits are common to the warp.
-__global__ void k_rho_partial(int N, int64_t S, const double* P, double* partials) {
-  __shared__ double s[HQ_THREADS / 32][HQ_MAXN];
+// y vary across the lanes (masked warp sums), higher bits are common to the warp.  The
+// sums are in 64-bit fixed point (P at 2^61; every partial sum is at most 1), so they
+// are exact integer adds rather than FP64 work.
+__device__ __forceinline__ long long warp_sum_q(long long v) {
+  for (int m = 16; m > 0; m >>= 1) v += __shfl_xor_sync(0xffffffffu, v, m);
+  return v;
+}
+
+__global__ void k_rho_partial(int N, int64_t S, const double* P, long long* partials) {
+  __shared__ long long s[HQ_THREADS / 32][HQ_MAXN];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  double acc[HQ_MAXN];
+  long long acc[HQ_MAXN];
 #pragma unroll
-  for (int i = 0; i < HQ_MAXN; i++) acc[i] = 0.0;
+  for (int i = 0; i < HQ_MAXN; i++) acc[i] = 0;
   const int64_t nwarps_total = (int64_t)gridDim.x * (blockDim.x >> 5);
   const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + wid;
   for (int64_t base = gw * 32; base < S; base += nwarps_total * 32) {
     int64_t y = base + lane;
-    double v = y < S ? P[y] : 0.0;
-    double tot = warp_sum_d(v);
+    const long long v = y < S ? __double2ll_rn(P[y] * 0x1p61) : 0;
+    const long long tot = warp_sum_q(v);
 #pragma unroll
     for (int i = 0; i < 5; i++) {
-      double t = warp_sum_d(((y >> i) & 1) ? v : 0.0);
+      const long long t = warp_sum_q(((y >> i) & 1) ? v : 0);
       if (i < N) acc[i] += t;
     }
 #pragma unroll
@@ -293,19 +341,19 @@ __global__ void k_rho_partial(int N, int64_t S, const double* P, double* partial
   }
   __syncthreads();
   if (threadIdx.x < N) {
-    double t = 0.0;
+    long long t = 0;
     for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += s[w][threadIdx.x];
     partials[(int64_t)blockIdx.x * HQ_MAXN + threadIdx.x] = t;
   }
 }
 
-__global__ void k_rho_final(int N, int nblk, const double* partials, const double* summary,
+__global__ void k_rho_final(int N, int nblk, const long long* partials, const double* summary,
                             double* rho) {
   int i = threadIdx.x;
   if (i >= N) return;
-  double t = 0.0;
+  long long t = 0;
   for (int b = 0; b < nblk; b++) t += partials[(int64_t)b * HQ_MAXN + i];
-  rho[i] = t + summary[5];  // queued states: every unit busy
+  rho[i] = (double)t * 0x1p-61 + summary[5];  // queued states: every unit busy
 }
 
 // h_i[X] = P{B} for B = X with a 0 inserted at bit i (unit i idle), in 64-bit fixed
@@ -362,12 +410,21 @@ __global__ void k_summary(int N, const double* nu, const double* rho, const doub
 template <class V>
 static int layer_sums_typed(hq_solver* h) {
   const typename V::T* p = (const typename V::T*)hq_bufs(h, V::kind).p;
-  for (int n = 0; n <= h->N; n++) {
-    int64_t Ln = h->lsize[n];
-    k_layer_sum<V><<<(unsigned)((Ln + 255) / 256), 256, 0, h->stream>>>(
-        n, Ln, h->masks + h->off[n], p + h->off[n], h->nu, h->partials, h->sc);
-    HQ_LAUNCHED();
-  }
+  LayerSumArgs a;
+  a.N = h->N;
+  for (int i = 0; i < HQ_MAXN + 2; i++) a.off[i] = h->off[i];
+  for (int i = 0; i <= HQ_MAXN; i++) a.lsize[i] = i <= h->N ? h->lsize[i] : 0;
+  int ex = 0;
+  frexp(h->nu_sum > 0.0 ? h->nu_sum : 1.0, &ex);  // sum nu < 2^ex: mu_m p < 2^61 at 2^(61-ex)
+  a.scale_nu = ldexp(1.0, 61 - ex);
+  HQ_CUDA(cudaMemsetAsync(h->sc->lsum_q, 0, sizeof(long long) * 2 * (HQ_MAXN + 1), h->stream));
+  const int64_t chunks = h->Sp >> 5;
+  const int64_t want = (chunks + 7) / 8;  // 8 warps per CTA
+  const unsigned grid = (unsigned)(want < 152 * 8 ? (want > 0 ? want : 1) : 152 * 8);
+  k_layer_sum<V><<<grid, 256, 0, h->stream>>>(a, h->masks, p, h->nu, h->sc);
+  HQ_LAUNCHED();
+  k_layer_totals<<<1, 32, 0, h->stream>>>(h->N, 1.0 / a.scale_nu, h->sc);
+  HQ_LAUNCHED();
   return HQ_OK;
 }
 
@@ -469,9 +526,9 @@ int hq_finalize(hq_solver* h, int prec, bool full_outputs, double* residual_out)
     HQ_LAUNCHED();
     int64_t want = (h->S + 255) / 256;
     int nblk = (int)(want < 152 * 8 ? want : 152 * 8);
-    k_rho_partial<<<nblk, 256, 0, h->stream>>>(h->N, h->S, h->P, h->partials);
+    k_rho_partial<<<nblk, 256, 0, h->stream>>>(h->N, h->S, h->P, (long long*)h->partials);
     HQ_LAUNCHED();
-    k_rho_final<<<1, 32, 0, h->stream>>>(h->N, nblk, h->partials, h->summary, h->rho);
+    k_rho_final<<<1, 32, 0, h->stream>>>(h->N, nblk, (const long long*)h->partials, h->summary, h->rho);
     HQ_LAUNCHED();
     if (h->N >= 2) {
       int64_t half = (int64_t)1 << (h->N - 1);
