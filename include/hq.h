@@ -259,13 +259,17 @@ int hq_dispatch_table_static(int N, int J, const double* lambda_j, const int32_t
  *   count entries; ms_total: NULL or the wall time.  Returns HQ_ENOTCONVERGED if some
  *   instance missed the tolerance, HQ_EDIVERGED, HQ_ETIMEOUT (a bounded device wait gave
  *   up) or HQ_ECUDA.  Calls on one batch, or on its solvers, must not overlap.
+ * hq_batch_set_variant: use kernel variant `variant` (0..3, as numbered for
+ *   hq_batch_tune) for `precision` (HQ_PREC_FP64, _DF64 or _FP32) in later solves,
+ *   instead of the tuned or default one.  Errors: HQ_EINVAL.
  * hq_batch_info: out8 = {count, largest N, states swept per sweep (sum of 2^N - 2), work
  *   items, graph state (1 replayed graph, -1 capture refused and direct launches, 0 not
- *   tried yet), tuned variant for FP64, DF64, FP32}. */
+ *   tried yet), variant in use for FP64, DF64, FP32}. */
 typedef struct hq_batch hq_batch;
 int hq_batch_create(hq_solver* const* solvers, int count, void* stream, hq_batch** out);
 int hq_batch_tune(hq_batch* b, int precision, int sweeps, int* variant_out, float* ms_out);
 int hq_batch_solve(hq_batch* b, const hq_opts* opts, hq_stats* stats, double* ms_total);
+int hq_batch_set_variant(hq_batch* b, int precision, int variant);
 int hq_batch_info(const hq_batch* b, int64_t* out8);
 void hq_batch_destroy(hq_batch* b);
 

@@ -611,6 +611,20 @@ extern "C" void hq_batch_destroy(hq_batch* b) {
   delete b;
 }
 
+extern "C" int hq_batch_set_variant(hq_batch* b, int precision, int variant) {
+  if (!b) { hq_set_error("NULL batch"); return HQ_EINVAL; }
+  if (precision != HQ_PREC_FP64 && precision != HQ_PREC_DF64 && precision != HQ_PREC_FP32) {
+    hq_set_error("precision must be FP64, DF64 or FP32");
+    return HQ_EINVAL;
+  }
+  if (variant < 0 || variant >= kVariants) {
+    hq_set_error("variant out of range");
+    return HQ_EINVAL;
+  }
+  b->variant[slot_of(precision)] = variant;
+  return HQ_OK;
+}
+
 extern "C" int hq_batch_info(const hq_batch* b, int64_t* out8) {
   if (!b || !out8) { hq_set_error("NULL argument"); return HQ_EINVAL; }
   out8[0] = b->K;

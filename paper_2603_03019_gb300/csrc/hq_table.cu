@@ -68,9 +68,11 @@ __global__ void k_histogram(int N, int J, const uint32_t* pre, const double* lam
 // passes handle groups of high bits with tiles made of 2^g strided rows of kCols
 // contiguous elements.
 // ---------------------------------------------------------------------------
-constexpr int kTileLog = 14;           // 16384 elements = 128 KB of shared memory per tile
-constexpr int kColsLog = 5;            // 32 contiguous elements (256 B) per row in later passes
-constexpr int kZetaThreads = 1024;
+constexpr int kLowLog = 12;            // first pass: tiles of 4096 contiguous elements (32 KB)
+constexpr int kLowThreads = 256;
+constexpr int kTileLog = 14;           // later passes: tiles of 16384 elements (128 KB)
+constexpr int kMinColsLog = 3;         // rows of at least 8 contiguous elements (64 B)
+constexpr int kHighThreads = 1024;
 
 __global__ void k_zeta_low(long long* buf, int bits, int tile_log, int64_t ntiles, bool superset) {
   extern __shared__ long long t[];
@@ -134,28 +136,32 @@ __global__ void k_zeta_high(long long* buf, int bits, int b0, int g, int cols_lo
   (void)bits;
 }
 
+// Pass 1 takes the low 12 bits; every later pass takes as many of the remaining bits as
+// fit a full 16384-element tile with rows of at least 8 contiguous elements, and widens
+// the rows when fewer bits remain (N=24: 12 + 11 bits in two passes; N=28: 12 + 11 + 4
+// with 1024-element rows), so no pass degenerates into many tiny tiles.
 int hq_zeta_subset(hq_solver* h, long long* buf, int bits, int count, bool superset) {
   if (bits <= 0) return HQ_OK;
   int64_t per = (int64_t)1 << bits;
-  int tl = bits < kTileLog ? bits : kTileLog;
+  int tl = bits < kLowLog ? bits : kLowLog;
   int64_t ntiles = (per >> tl) * count;
   size_t smem = sizeof(long long) << tl;
   const int smax = (int)(sizeof(long long) << kTileLog);
   HQ_CUDA(cudaFuncSetAttribute(k_zeta_low, cudaFuncAttributeMaxDynamicSharedMemorySize, smax));
   HQ_CUDA(cudaFuncSetAttribute(k_zeta_high, cudaFuncAttributeMaxDynamicSharedMemorySize, smax));
-  k_zeta_low<<<(unsigned)ntiles, kZetaThreads, smem, h->stream>>>(buf, bits, tl, ntiles, superset);
+  k_zeta_low<<<(unsigned)ntiles, kLowThreads, smem, h->stream>>>(buf, bits, tl, ntiles, superset);
   HQ_LAUNCHED();
   int b0 = tl;
   while (b0 < bits) {
     int g = bits - b0;
-    int cols_log = kColsLog < b0 ? kColsLog : b0;
-    int gmax = kTileLog - cols_log;
-    if (g > gmax) g = gmax;
+    if (g > kTileLog - kMinColsLog) g = kTileLog - kMinColsLog;
+    int cols_log = kTileLog - g;
+    if (cols_log > b0) cols_log = b0;
     int64_t colblocks = ((int64_t)1 << b0) >> cols_log;
     int64_t above = per >> (b0 + g);
     int64_t tpa = colblocks * above;
     size_t sm = sizeof(long long) << (g + cols_log);
-    k_zeta_high<<<(unsigned)(tpa * count), kZetaThreads, sm, h->stream>>>(buf, bits, b0, g, cols_log, per,
+    k_zeta_high<<<(unsigned)(tpa * count), kHighThreads, sm, h->stream>>>(buf, bits, b0, g, cols_log, per,
                                                                 tpa, count, superset);
     HQ_LAUNCHED();
     b0 += g;

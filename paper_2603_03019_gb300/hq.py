@@ -83,6 +83,7 @@ _SIGS = {
     "hq_batch_tune": (_i, [_vp, _i, _i, _vp, _vp]),
     "hq_batch_solve": (_i, [_vp, ctypes.POINTER(hq_opts), _vp, _vp]),
     "hq_batch_info": (_i, [_vp, _vp]),
+    "hq_batch_set_variant": (_i, [_vp, _i, _i]),
     "hq_batch_destroy": (None, [_vp]),
     "hq_mlp_create": (_i, [_i, ctypes.c_uint64, _vp, ctypes.POINTER(_vp)]),
     "hq_mlp_num_params": (ctypes.c_int64, [_vp]),
@@ -276,6 +277,10 @@ def hq_batch_solve(b: int, count: int, opts: hq_opts | None = None,
                                ctypes.addressof(st), ms.ctypes.data)
     _check(rc, allow)
     return rc, [st[i].as_dict() for i in range(count)], float(ms[0])
+
+
+def hq_batch_set_variant(b: int, precision: int, variant: int) -> None:
+    _check(load().hq_batch_set_variant(b, precision, variant))
 
 
 def hq_batch_info(b: int) -> np.ndarray:

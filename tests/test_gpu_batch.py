@@ -121,6 +121,30 @@ def test_batch_tune_and_uneven_n12_18(gpu_lib):
         s.close()
 
 
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+def test_batch_every_cta_shape_matches_oracle(gpu_lib, variant):
+    """Each kernel variant the autotuner may pick (threads per CTA x CTAs per SM) solves
+    the mixed batch to the oracle's answer."""
+    insts = _instances()
+    solvers = [hq.Solver.for_instance(i) for i in insts]
+    b = hq.hq_batch_create([s.h for s in solvers])
+    for prec in (hq.HQ_PREC_FP32, hq.HQ_PREC_DF64, hq.HQ_PREC_FP64):
+        hq.hq_batch_set_variant(b, prec, variant)
+    info = hq.hq_batch_info(b)
+    assert list(info[5:8]) == [variant] * 3
+    rc, stats, _ = hq.hq_batch_solve(b, len(insts), _opts("fp32+df64", 1e-13))
+    assert rc == hq.HQ_OK
+    for inst, s, st in zip(insts, solvers, stats):
+        assert st["converged"] == 1
+        r = oracle.solve(inst, eps=1e-15)
+        assert np.max(np.abs(s.stationary() - r["P"])) < 1e-10, inst.name
+    with pytest.raises(hq.HQError):
+        hq.hq_batch_set_variant(b, hq.HQ_PREC_FP32, 4)
+    hq.hq_batch_destroy(b)
+    for s in solvers:
+        s.close()
+
+
 def test_batch_errors(gpu_lib):
     inst = _instances()[0]
     unloaded = hq.Solver(inst.N, inst.J, inst.mode, inst.C)
