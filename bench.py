@@ -530,8 +530,9 @@ def run_batch(args):
 
 def run_warmstart(args):
     """Held-out instances (seeds never used in training), N = 16..22, J = 300: sweeps and
-    wall time to a 1e-10 relative balance residual from the paper's uniform start and
-    from the learned start (with its fallback), same solver, same GPU."""
+    wall time to a 1e-10 relative balance residual from the paper's uniform start, from
+    the analytic product-form start (first-choice utilisations, the control) and from the
+    learned start (both with their fallback), same solver, same GPU."""
     import torch
 
     from paper_2603_03019_gb300 import hq
@@ -545,11 +546,13 @@ def run_warmstart(args):
             s = hq.Solver.for_instance(inst)
             hq.hq_attach_mlp(s.h, m)
             res = {}
-            for name, warm in (("cold", False), ("learned", True)):
-                s.solve(tol=args.tol, precision=args.precision, warm_mlp=warm)  # warm-up
+            for name, warm, analytic in (("cold", False, False), ("analytic", False, True),
+                                         ("learned", True, False)):
+                s.solve(tol=args.tol, precision=args.precision, warm_mlp=warm, warm_product=analytic)
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
-                rc, st = s.solve(tol=args.tol, precision=args.precision, warm_mlp=warm)
+                rc, st = s.solve(tol=args.tol, precision=args.precision, warm_mlp=warm,
+                                 warm_product=analytic)
                 torch.cuda.synchronize()
                 res[name] = {"ms": 1000 * (time.perf_counter() - t0),
                              "sweeps": st["sweeps_fp32"] + st["sweeps_hi"],
@@ -566,6 +569,9 @@ def run_warmstart(args):
                        "precision": args.precision, "tol": args.tol},
             "sweeps_cold": sum(r["cold"]["sweeps"] for r in rows),
             "sweeps_learned": sum(r["learned"]["sweeps"] for r in rows),
+            "sweeps_analytic": sum(r["analytic"]["sweeps"] for r in rows),
+            "time_ratio_analytic": cold / sum(r["analytic"]["ms"] for r in rows),
+            "kept": {k: sum(r[k]["warm_used"] for r in rows) for k in ("analytic", "learned")},
             "rows": rows}
     print(json.dumps(line))
     return 0

@@ -75,7 +75,7 @@ typedef enum {
   HQ_TOL_RESIDUAL = 1  /* max_m |out_m - in_m| / max_m out_m of Eq. (1) <= tol, FP64 */
 } hq_tol_kind;
 
-typedef enum { HQ_WARM_NONE = 0, HQ_WARM_GIVEN = 1, HQ_WARM_MLP = 2 } hq_warm;
+typedef enum { HQ_WARM_NONE = 0, HQ_WARM_GIVEN = 1, HQ_WARM_MLP = 2, HQ_WARM_PRODUCT = 3 } hq_warm;
 
 typedef struct hq_opts {
   double tol;          /* stopping tolerance (see tol_kind) */
@@ -283,6 +283,10 @@ void hq_batch_destroy(hq_batch* b);
  * p_n(B) = prod_{i in B} x_i(n) / e_n(x(n)), x_i(n) = q_i(n) / (1 - q_i(n)), and keeps it
  * only if its first sweep's step is no larger than that of a first sweep from the uniform
  * start (both probe sweeps are counted in the stats; stats.warm_used says which won).
+ * warm_start = HQ_WARM_PRODUCT is the analytic control, with no network: the same
+ * product form and fallback with q_i(n) = rho0_i for every layer, rho0_i the unit's
+ * first-choice utilisation lambda1_i / nu_i clipped to [0.02, 0.98], lambda1_i the
+ * demand of the nodes that rank unit i first (so x_i = rho0_i / (1 - rho0_i)).
  *
  * Network, weights shared across units and layers: 9 -> hidden (ReLU) -> hidden (ReLU)
  * -> 1, the output estimating logit(q_i(n)); activations stored in BF16, the hidden x

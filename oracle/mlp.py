@@ -155,6 +155,23 @@ def layer_law(q: np.ndarray, lam: float, nu: np.ndarray) -> tuple[np.ndarray, np
     return P, P @ q
 
 
+def first_choice_start(inst) -> tuple[np.ndarray, np.ndarray]:
+    """The analytic start (no network): rho0_i = lambda1_i / nu_i clipped to
+    [0.02, 0.98], lambda1_i = sum of lambda_j over the nodes j whose first choice is
+    unit i; q_i(n) = rho0_i for every layer 1..N-1 (0 in layer 0, 1 in layer N), with q
+    passed through the same float32 logit as the GPU's logit buffer.  Returns (rho0, q)."""
+    N = inst.N
+    l1 = np.zeros(N)
+    for j in range(inst.J):
+        l1[int(inst.pref[j, 0])] += inst.lam_j[j]
+    rho0 = np.clip(l1 / np.asarray(inst.nu, dtype=np.float64), 0.02, 0.98)
+    y = np.log(rho0 / (1.0 - rho0)).astype(np.float32).astype(np.float64)
+    q = np.zeros((N + 1, N))
+    q[N] = 1.0
+    q[1:N] = 1.0 / (1.0 + np.exp(-y))
+    return rho0, q
+
+
 def conditional_occupancy(cond: np.ndarray, N: int) -> np.ndarray:
     """q_i(n) = sum of p_n(B) over the states B of layer n with unit i busy."""
     S = 1 << N

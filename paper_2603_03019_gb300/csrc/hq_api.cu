@@ -282,6 +282,7 @@ extern "C" int hq_solve(hq_solver* h, const hq_opts* opts_in, hq_stats* stats) {
   if (o.max_sweeps < 0) { hq_set_error("max_sweeps must be >= 0"); return HQ_EINVAL; }
   if (o.precision < HQ_PREC_FP64 || o.precision > HQ_PREC_FP32_IR) { hq_set_error("bad precision"); return HQ_EINVAL; }
   if (o.tol_kind != HQ_TOL_STEP && o.tol_kind != HQ_TOL_RESIDUAL) { hq_set_error("bad tol_kind"); return HQ_EINVAL; }
+  if (o.warm_start < HQ_WARM_NONE || o.warm_start > HQ_WARM_PRODUCT) { hq_set_error("bad warm_start"); return HQ_EINVAL; }
   if (o.warm_start == HQ_WARM_GIVEN && !o.warm_p) { hq_set_error("warm_p is NULL"); return HQ_EINVAL; }
   if (o.warm_start == HQ_WARM_MLP && !h->mlp) { hq_set_error("no warm-start model is attached"); return HQ_EINVAL; }
   // FP32 sweeps stall at their rounding floor; leaving them a check early costs little
@@ -316,15 +317,17 @@ extern "C" int hq_solve(hq_solver* h, const hq_opts* opts_in, hq_stats* stats) {
   int total = 0, checks = 0, res_checks = 0, since_res = 0, stalled = 0;
   bool warm_kept = o.warm_start == HQ_WARM_GIVEN;
   int rc;
-  if (o.warm_start == HQ_WARM_MLP && h->N >= 2) {
-    // the learned start is kept only if its first sweep moves the iterate no more than
-    // a first sweep from the paper's uniform start does; both probe sweeps are counted
+  if ((o.warm_start == HQ_WARM_MLP || o.warm_start == HQ_WARM_PRODUCT) && h->N >= 2) {
+    // the learned (or analytic) start is kept only if its first sweep moves the iterate
+    // no more than a first sweep from the paper's uniform start does; both probe sweeps
+    // are counted
     rc = hq_init_iterate(h, phases[0], nullptr, HQ_HOST);
     if (rc == HQ_OK) rc = hq_run_sweeps(h, phases[0], 1, nullptr, nullptr);
     if (rc == HQ_OK) rc = pull_scalars(h);
     if (rc != HQ_OK) return rc;
     const double step_cold = h->hsc->step;
-    rc = hq_mlp_warm_start(h, h->mlp, h->pcond, nullptr);
+    rc = o.warm_start == HQ_WARM_MLP ? hq_mlp_warm_start(h, h->mlp, h->pcond, nullptr)
+                                     : hq_product_warm_start(h, h->pcond);
     if (rc == HQ_OK) rc = hq_init_iterate(h, phases[0], h->pcond, HQ_DEVICE);
     if (rc == HQ_OK) rc = hq_run_sweeps(h, phases[0], 1, nullptr, nullptr);
     if (rc == HQ_OK) rc = pull_scalars(h);

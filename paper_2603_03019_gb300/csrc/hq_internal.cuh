@@ -290,6 +290,7 @@ int hq_build_rates(hq_solver* h);  // r_m in all precisions
 int hq_mlp_predict_dev(hq_mlp* m, const float* X, int B, float* y_dev, cudaStream_t s);
 int hq_mlp_features_dev(hq_solver* h, float* X);
 int hq_mlp_warm_start(hq_solver* h, hq_mlp* m, double* P, double* rho);
+int hq_product_warm_start(hq_solver* h, double* P);  // the analytic control (HQ_WARM_PRODUCT)
 
 // refinement (hq_refine.cu): correction sweeps run as sweep precision HQ_PREC_IRC on
 // the FP32 buffers; hq_ir_begin sets up a base from the iterate held in precision

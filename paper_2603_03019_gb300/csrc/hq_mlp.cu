@@ -604,6 +604,37 @@ __global__ void k_product_fill(int N, int64_t S, const double* lx, const double*
 
 }  // namespace
 
+// the analytic control: logit(rho0_i) for every layer, rho0_i = lambda1_i / nu_i clipped
+// to [0.02, 0.98], lambda1_i the demand of the nodes ranking unit i first (summed in
+// node order)
+__global__ void k_analytic_logits(int N, int J, const double* lam_j, const int32_t* pref, const double* nu,
+                                  float* y) {
+  if (threadIdx.x != 0) return;
+  double l1[HQ_MAXN];
+  for (int i = 0; i < N; i++) l1[i] = 0.0;
+  for (int j = 0; j < J; j++) l1[pref[(int64_t)j * N]] += lam_j[j];
+  for (int i = 0; i < N; i++) {
+    const double r = fmin(fmax(l1[i] / nu[i], 0.02), 0.98);
+    const float l = (float)log(r / (1.0 - r));
+    for (int n = 1; n <= N - 1; n++) y[(size_t)(n - 1) * N + i] = l;
+  }
+}
+
+int hq_product_warm_start(hq_solver* h, double* P) {
+  if (!h->wy || h->N < 2) {
+    hq_set_error("solver scratch for the warm start is missing");
+    return HQ_ESTATE;
+  }
+  k_analytic_logits<<<1, 32, 0, h->stream>>>(h->N, h->J, h->lam_j, h->pref, h->nu, h->wy);
+  HQ_LAUNCHED();
+  double* le = h->wlx + (size_t)HQ_MAXN * HQ_MAXN;
+  k_product_norm<<<1, 32, 0, h->stream>>>(h->N, h->wy, h->wlx, le);
+  HQ_LAUNCHED();
+  k_product_fill<<<(unsigned)((h->S + 255) / 256), 256, 0, h->stream>>>(h->N, h->S, h->wlx, le, P);
+  HQ_LAUNCHED();
+  return HQ_OK;
+}
+
 int hq_mlp_features_dev(hq_solver* h, float* X) {
   k_features<<<1, 32, 0, h->stream>>>(h->N, h->J, h->lam_j, h->pref, h->nu, h->lam, h->nu_sum, X);
   HQ_LAUNCHED();

@@ -21,7 +21,7 @@ HQ_LOSS, HQ_FINITE, HQ_INFINITE = 0, 1, 2
 HQ_HOST, HQ_DEVICE = 0, 1
 HQ_PREC_FP64, HQ_PREC_DF64, HQ_PREC_FP32, HQ_PREC_FP32_DF64, HQ_PREC_FP32_FP64, HQ_PREC_FP32_IR = 0, 1, 2, 3, 4, 5
 HQ_TOL_STEP, HQ_TOL_RESIDUAL = 0, 1
-HQ_WARM_NONE, HQ_WARM_GIVEN, HQ_WARM_MLP = 0, 1, 2
+HQ_WARM_NONE, HQ_WARM_GIVEN, HQ_WARM_MLP, HQ_WARM_PRODUCT = 0, 1, 2, 3
 
 PRECISION = {"fp64": HQ_PREC_FP64, "df64": HQ_PREC_DF64, "fp32": HQ_PREC_FP32,
              "fp32+df64": HQ_PREC_FP32_DF64, "fp32+fp64": HQ_PREC_FP32_FP64, "fp32+ir": HQ_PREC_FP32_IR}
@@ -407,7 +407,7 @@ class Solver:
         hq_load(self.h, lam_j, nu, pref)
 
     def solve(self, tol=1e-10, tol_kind=HQ_TOL_RESIDUAL, precision="fp32+df64", max_sweeps=100000,
-              check_every=8, warm_p=None, fp32_stall=0.0, warm_mlp=False,
+              check_every=8, warm_p=None, fp32_stall=0.0, warm_mlp=False, warm_product=False,
               omega=1.0) -> tuple[int, dict]:
         o = hq_default_opts()
         o.tol = tol
@@ -427,6 +427,8 @@ class Solver:
             o.warm_mem = m
         elif warm_mlp:
             o.warm_start = HQ_WARM_MLP
+        elif warm_product:
+            o.warm_start = HQ_WARM_PRODUCT
         rc, st = hq_solve(self.h, o)
         del keep
         return rc, st.as_dict()

@@ -119,6 +119,36 @@ def test_learned_start_is_the_layer_product_form(gpu_lib, seed):
     assert np.max(np.abs(g - want)) < 1e-12
 
 
+@pytest.mark.parametrize("seed", [14, 15, 16])
+def test_analytic_start_is_the_layer_product_form(gpu_lib, seed):
+    """The analytic control (first-choice utilisations, no network) after its two probe
+    sweeps: one FP64 sweep of Algorithm 1 (oracle) from the oracle's product form of
+    the same q if it was kept, else the uniform start; and it solves to the same answer."""
+    import oracle
+    inst = I.warmstart_instance(200 + seed, N=9, J=60)
+    s = hq.Solver.for_instance(inst)
+    rc, st = s.solve(tol=0.0, tol_kind=hq.HQ_TOL_STEP, precision="fp64", max_sweeps=2, check_every=1,
+                     warm_product=True)
+    g = s.conditional()
+    assert st["sweeps_hi"] == 2
+    _, q = ref.first_choice_start(inst)
+    if st["warm_used"]:
+        o = oracle.Oracle(inst)
+        o.build_table()
+        o.init(ref.product_form_layers(q))
+        o.sweep(1e-20)
+        want = o.conditional()
+        o.close()
+    else:
+        want = np.array([1.0 / math.comb(inst.N, bin(b).count("1")) for b in range(1 << inst.N)])
+    assert np.max(np.abs(g - want)) < 1e-12
+    rc, st = s.solve(tol=1e-13, precision="fp32+ir", omega=-1.0, warm_product=True)
+    assert rc == hq.HQ_OK
+    r = oracle.solve(inst, eps=1e-15)
+    assert np.max(np.abs(s.stationary() - r["P"])) < 1e-10
+    s.close()
+
+
 def test_learned_start_reaches_the_same_solution(gpu_lib):
     inst = I.warmstart_instance(321, N=12, J=100)
     m = hq.hq_mlp_create(H, 13)  # untrained: the solve must still be exact

@@ -72,6 +72,19 @@ def test_features_by_hand():
             assert np.allclose(X[(n - 1) * 3 + i], np.concatenate([u[i], [n / 3]]), rtol=1e-6, atol=1e-7)
 
 
+def test_first_choice_start_by_hand():
+    inst = I.geometric_instance(3, 3, 7, 0.5, nu_lo=0.5, nu_hi=1.5)
+    inst.lam_j = np.array([0.3, 0.9, 2.0])
+    inst.nu = np.array([1.0, 2.0, 3.0])
+    inst.pref = np.array([[2, 0, 1], [2, 1, 0], [0, 1, 2]], dtype=np.int32)
+    rho0, q = mlp.first_choice_start(inst)
+    # unit 0: node 2 (2.0 / 1.0, clipped to 0.98); unit 1: nobody (0, clipped to 0.02);
+    # unit 2: nodes 0 and 1 ((0.3 + 0.9) / 3)
+    assert np.allclose(rho0, [0.98, 0.02, 0.4], rtol=0, atol=1e-15)
+    assert np.all(q[0] == 0) and np.all(q[3] == 1)
+    assert np.allclose(q[1], rho0, rtol=1e-7) and np.array_equal(q[1], q[2])
+
+
 def test_product_form_special_cases():
     N = 6
     q = np.full((N + 1, N), 0.5)
