@@ -37,6 +37,8 @@ sys.path.insert(0, ROOT)
 from paper_2603_03019_gb300 import instances as I  # noqa: E402
 
 WORKLOADS = {
+    "n28": lambda seed: I.large_infinite_n24(seed, N=28),
+    "n26": lambda seed: I.large_infinite_n24(seed, N=26),
     "n24": lambda seed: I.large_infinite_n24(seed),
     "n23": lambda seed: I.large_infinite_n24(seed, N=23),
     "n22": lambda seed: I.large_infinite_n24(seed, N=22),
@@ -57,7 +59,7 @@ TRAFFIC_SOURCE = ("ncu --set full of one FP32 sweep at N=22 (profiles/k_persist_
                   "298.5 MB DRAM for 251.7 MB algorithmic, scaled by algorithmic bytes")
 METRIC = ("state-updates/s (solve to 1e-10 relative balance residual; N=24 time-to-tol, "
           "FP32+refinement vs plain FP64, reported beside it)")
-BASE_SEED = {"n24": 3001, "n23": 3001, "n22": 3001, "n20": 2001, "n10": 1001}
+BASE_SEED = {"n28": 3001, "n26": 3001, "n24": 3001, "n23": 3001, "n22": 3001, "n20": 2001, "n10": 1001}
 
 
 def parse():
