@@ -55,7 +55,7 @@ WORKLOADS = {
 DTYPE = {"fp32+ir": "f32 sweeps + f64 refinement base", "fp32+df64": "f32 + df64 sweeps",
          "fp32+fp64": "f32 + f64 sweeps", "fp64": "f64", "df64": "df64", "fp32": "f32"}
 SWEEP_DRAM_PER_ALG_BYTE = 298.461e6 / 251658120
-TRAFFIC_SOURCE = ("ncu --set full of one FP32 sweep at N=22 (profiles/k_persist_fp32_n22_set_full.md): "
+TRAFFIC_SOURCE = ("ncu --set full of one FP32 sweep at N=22 (the k_persist FP32 N=22 summary): "
                   "298.5 MB DRAM for 251.7 MB algorithmic, scaled by algorithmic bytes")
 METRIC = ("state-updates/s (solve to 1e-10 relative balance residual; N=24 time-to-tol, "
           "FP32+refinement vs plain FP64, reported beside it)")
