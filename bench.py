@@ -246,12 +246,13 @@ def run_reference(args):
     total = sum(times)
     value = states * len(times) / total
     line = {"metric": METRIC, "value": value,
-            "unit": "state-updates/s", "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+            "unit": "state-updates/s", "n_gpus": ws if ws > 1 else args.gpus, "steps": args.steps,
+            "warmup": args.warmup,
             "ms_per_step": 1000 * total / len(times), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": inst.name, "N": N, "J": inst.J, "mode": "infinite",
-                       "sample": f"layer {n} update per step"},
+            "config": {"workload": inst.name, "N": N, "J": inst.J, "mode": I.MODE_NAMES[inst.mode],
+                       "sample": f"layer {n} update per step", "device": "host CPU, one core"},
             "cpu_baseline": {"value": value, "unit": "state-updates/s", "cores": 1,
                              "kind": "oracle",
                              "sample": f"one Algorithm-1 update of layer {n} ({states} states) "
