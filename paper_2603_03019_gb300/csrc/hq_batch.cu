@@ -81,7 +81,7 @@ struct BatchArgs {
   const uint4* folds;       // {instance, first item, end item, 0}
   double* ipart;            // 4 partial sums per item
   unsigned* step_bits;      // [2][K] FP32 bit patterns of the per-sweep step maxima
-  unsigned* bar;            // [0] arrivals, [1] generation, [2] flags
+  unsigned* bar;            // [0] arrivals, [1] (unused), [2] flags
 };
 
 template <class V, int kThreads>
@@ -97,7 +97,6 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_batch(BatchArgs a
   __shared__ double s_red[4][kWarps];
   __shared__ uint32_t s_hl[kWarps][32];  // per warp: the item's high-part neighbour bases
   __shared__ T s_hnu[kWarps][32];        // and its idle high-part units' rates
-  __shared__ unsigned s_gen0;
 
   const unsigned G = gridDim.x;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -128,7 +127,6 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_batch(BatchArgs a
     }
     s_bin[L][i % (HQ_LO_BITS + 2)] = c;
   }
-  if (threadIdx.x == 0) s_gen0 = ld_relaxed_u32(&a.bar[1]);
   __syncthreads();
 
   const int gwarp = (int)blockIdx.x * kWarps + wid;
@@ -137,24 +135,22 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_batch(BatchArgs a
   const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   int gbar = 0;  // grid barriers passed in this launch
 
+  // grid barrier: released arrivals on a counter (zeroed before the launch); every CTA
+  // waits until the count of barrier g reaches G (g + 1)
   auto grid_barrier = [&]() {
     __syncthreads();
     if (threadIdx.x == 0) {
-      const unsigned old = atom_add_acq_rel(&a.bar[0], 1u);
-      if (old == G * (unsigned)(gbar + 1) - 1u) {
-        red_add_release(&a.bar[1], 1u);
-      } else {
-        const unsigned target = s_gen0 + (unsigned)gbar + 1u;
-        unsigned it = 0;
-        while ((int)(ld_relaxed_u32(&a.bar[1]) - target) < 0) {
-          if (*(volatile unsigned*)&a.bar[2] & 2u) break;
-          if (++it > kSpinLimit) {
-            atomicOr(&a.bar[2], 2u);
-            break;
-          }
+      red_add_release(&a.bar[0], 1u);
+      const unsigned target = G * (unsigned)(gbar + 1);
+      unsigned it = 0;
+      while ((int)(ld_relaxed_u32(&a.bar[0]) - target) < 0) {
+        if (*(volatile unsigned*)&a.bar[2] & 2u) break;
+        if (++it > kSpinLimit) {
+          atomicOr(&a.bar[2], 2u);
+          break;
         }
-        fence_acq_rel_gpu();
       }
+      fence_acq_rel_gpu();
     }
     __syncthreads();
     gbar++;
