@@ -121,16 +121,20 @@ typedef struct hq_stats {
 
 typedef struct hq_solver hq_solver;
 
-/* Fill opts with defaults: tol 1e-10 on the residual, FP32 then DF64 sweeps,
- * check every 8 sweeps, max 100000 sweeps, cold start. */
+/* Fill opts with defaults: tol 1e-10 on the residual, FP32 then DF64 sweeps (valid
+ * for single and batched solves; HQ_PREC_FP32_IR is faster for single solves), check
+ * every 8 sweeps, max 100000 sweeps, omega 1, cold start. */
 void hq_default_opts(hq_opts* opts);
 
 /* Allocate a solver for N units (1..28), J nodes (>= 1) and a queue mode
  * (capacity_C >= 1 iff HQ_FINITE, ignored otherwise) on the current device.
  * stream: a cudaStream_t, or NULL for the default stream.  Allocates every device
- * buffer the solve needs (about 16 N 2^N + 48 2^N bytes plus a (N/2) 2^N FP32
- * table, e.g. 4.3 GB at N=24).  Builds the N-dependent layout (layer-ranked
- * state masks and rank tables).  Writes the handle to *out. */
+ * buffer the solve needs: about 14 N 2^N bytes for the upward-rate table in FP64,
+ * double-float and FP32 and the transform scratch, plus about 104 bytes per state
+ * (masks, neighbour positions, iterates and r in three precisions, the refinement's
+ * base and base terms, the outputs); e.g. 7.4 GB at N=24, 130 GB at N=28.  Builds
+ * the N-dependent layout (layer-ranked state masks and rank tables).  Writes the
+ * handle to *out. */
 int hq_create(int N, int J, int mode, int capacity_C, void* stream, hq_solver** out);
 
 /* Load an instance (Section 2.1) and build its upward-rate table (Eq. 3).
