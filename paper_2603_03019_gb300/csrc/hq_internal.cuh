@@ -167,7 +167,6 @@ struct DevScalars {
   int flags;                   // bit 0: non-finite value seen
   unsigned ticket[4];          // last-block tickets
   unsigned bar_count;          // grid barrier of the persistent sweep kernel: arrivals
-  unsigned bar_gen;            // (unused; kept for the layout)
   double red[16];              // results of whole-vector reductions
   double lsum[HQ_MAXN + 1];    // sum_m p_n(B_m) per layer (whole-vector pass)
   double lmu[HQ_MAXN + 1];     // sum_m mu_m p_n(B_m) per layer
@@ -177,7 +176,6 @@ struct DevScalars {
   double res_den[HQ_MAXN + 1]; // max_m out_m per layer
   double fac[HQ_MAXN + 1];     // P{B} = fac[w(B)] * p_w(B) after the birth-death step
   double lam;                  // lambda = sum_j lambda_j of the loaded instance
-  double pub[2][8];            // (unused; kept for the layout)
   // refinement (correction sweeps against an FP64 base p0): the base's layer scalars
   // c1^0(n), c2^0(n) and its per-layer sums {sum mu A0, sum mu B0, sum A0, sum B0}
   double ir_c1[HQ_MAXN + 1];
