@@ -252,7 +252,7 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_batch(BatchArgs a
 #pragma unroll
           for (int w = 0; w < 4; w++) {
             f[w] = lane < kWarps ? s_red[w][lane] : 0.0;
-            for (int m = kWarps / 2; m > 0; m >>= 1) f[w] += __shfl_xor_sync(0xffffffffu, f[w], m);
+            for (int m = 16; m > 0; m >>= 1) f[w] += __shfl_xor_sync(0xffffffffu, f[w], m);  // lanes past kWarps hold 0
           }
           if (lane == 0) {
             // closed-form limit of the inner loop (Eq. 12 and 14), then Eq. (13)

@@ -201,7 +201,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_persist(PersistArgs a) {
       for (int w = 0; w < 5; w++) v[w] = lane < kWarps ? s_red[w][lane] : 0.0;
 #pragma unroll
       for (int w = 0; w < 5; w++)
-        for (int m = kWarps / 2; m > 0; m >>= 1) {
+        for (int m = 16; m > 0; m >>= 1) {  // lanes past kWarps hold 0
           const double o = __shfl_xor_sync(0xffffffffu, v[w], m);
           v[w] = (w == 4) ? fmax(v[w], o) : v[w] + o;
         }
