@@ -441,7 +441,11 @@ int hq_run_sweeps(hq_solver* h, int prec, int nsweeps, cudaEvent_t ev0, cudaEven
   h->it_version++;
   // the barrier's arrival count (grid size x phases of a launch) stays below 2^31
   const int64_t per = ((int64_t)1 << 31) / ((int64_t)152 * 8 * (h->N - 1) + 1) - 1;
-  const int cap = per > (1 << 20) ? (1 << 20) : (per < 1 ? 1 : (int)per);
+  // Layer N-1 of a sweep is finalised lazily in phase 1 of the next sweep of the same
+  // launch, whose gather of layer 1 reads layer 2; for N = 3 those are the same layer, so
+  // there every launch runs one sweep (its closing phase finalises layer N-1, and a
+  // launch's first phase finalises nothing)
+  const int cap = h->N == 3 ? 1 : (per > (1 << 20) ? (1 << 20) : (per < 1 ? 1 : (int)per));
   for (int done = 0; done < nsweeps;) {
     const int k = nsweeps - done < cap ? nsweeps - done : cap;
     cudaEvent_t e0 = done == 0 ? ev0 : nullptr, e1 = done + k == nsweeps ? ev1 : nullptr;
