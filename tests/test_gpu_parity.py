@@ -135,30 +135,33 @@ def test_fp32_only_bound(gpu_lib):
 
 # ---- degenerate cases --------------------------------------------------------------------
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32+ir"])
 @pytest.mark.parametrize("mode,C", [(0, 0), (1, 3), (2, 0)])
-def test_single_unit(gpu_lib, mode, C):
+def test_single_unit(gpu_lib, mode, C, prec):
     inst = I.Instance(N=1, J=1, lam_j=np.array([0.7]), nu=np.array([1.3]),
                       pref=np.array([[0]], np.int32), mode=mode, C=C)
-    g = _solve_gpu(inst, precision="fp64")
+    g = _solve_gpu(inst, precision=prec)
     r = oracle.solve(inst, eps=1e-15)
     assert np.max(np.abs(g["P"] - r["P"])) < 1e-14
     assert np.max(np.abs(g["pn"] - r["pn"])) < 1e-14
     assert np.max(np.abs(g["R"] - r["R"])) < 1e-14
 
 
-def test_two_units_golden(gpu_lib):
+@pytest.mark.parametrize("prec", ["fp64", "fp32+ir", "fp32+df64"])
+def test_two_units_golden(gpu_lib, prec):
     inst = I.Instance(N=2, J=2, lam_j=np.array([1.0, 2.0]), nu=np.array([1.0, 2.0]),
                       pref=np.array([[0, 1], [1, 0]], np.int32))
-    g = _solve_gpu(inst, tol=1e-15, tol_kind=hq.HQ_TOL_STEP, precision="fp64")
+    g = _solve_gpu(inst, tol=1e-15, tol_kind=hq.HQ_TOL_STEP, precision=prec)
     assert np.max(np.abs(g["P"] - np.array([18, 24, 15, 39]) / 96.0)) < 1e-14
 
 
 def test_zero_rate_nodes_and_single_node(gpu_lib):
     inst = I.geometric_instance(9, 20, 31, 0.6, nu_lo=0.5, nu_hi=1.5)
     inst.lam_j[::3] = 0.0
-    g = _solve_gpu(inst, tol=1e-13, precision="df64")
-    r = oracle.solve(inst, eps=1e-15)
-    assert np.max(np.abs(g["P"] - r["P"])) < 1e-10
+    for prec in ("df64", "fp32+ir"):
+        g = _solve_gpu(inst, tol=1e-13, precision=prec)
+        r = oracle.solve(inst, eps=1e-15)
+        assert np.max(np.abs(g["P"] - r["P"])) < 1e-10, prec
     one = I.Instance(N=7, J=1, lam_j=np.array([3.0]), nu=np.linspace(0.5, 1.5, 7),
                      pref=np.array([[3, 1, 4, 0, 5, 2, 6]], np.int32))
     g1 = _solve_gpu(one, tol=1e-13, precision="df64")
