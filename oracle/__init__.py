@@ -30,8 +30,9 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "hq_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_LIB_OMP_PATH = os.path.join(_BUILD, "liboracle_omp.so")
 _lock = threading.Lock()
-_lib = None
+_libs: dict = {}
 
 _d = ctypes.c_double
 _i = ctypes.c_int
@@ -43,26 +44,49 @@ _pu64 = ctypes.POINTER(ctypes.c_uint64)
 _vp = ctypes.c_void_p
 
 
-def build(force: bool = False) -> str:
-    """Compile hq_oracle.c into oracle/_build/liboracle.so (gcc, -O2, no fast-math)."""
+def _compile(path: str, omp: bool, force: bool) -> str:
     os.makedirs(_BUILD, exist_ok=True)
-    stale = (not os.path.exists(_LIB_PATH)
-             or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC))
+    stale = not os.path.exists(path) or os.path.getmtime(path) < os.path.getmtime(_SRC)
     if force or stale:
-        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        tmp = path + f".tmp{os.getpid()}"
         cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fno-fast-math",
-               "-ffp-contract=off", _SRC, "-o", tmp, "-lm"]
+               "-ffp-contract=off", *(["-fopenmp"] if omp else []), _SRC, "-o", tmp, "-lm"]
         subprocess.run(cmd, check=True)
-        os.replace(tmp, _LIB_PATH)
+        os.replace(tmp, path)
+    return path
+
+
+def build(force: bool = False) -> str:
+    """Compile hq_oracle.c (gcc, -O2, no fast-math) twice: plainly into
+    oracle/_build/liboracle.so (single-threaded) and with -fopenmp into
+    liboracle_omp.so (the loops over the states of a layer on all host threads).  A
+    toolchain without OpenMP support leaves only the plain library."""
+    _compile(_LIB_PATH, False, force)
+    try:
+        _compile(_LIB_OMP_PATH, True, force)
+    except (subprocess.CalledProcessError, OSError):
+        pass
     return _LIB_PATH
 
 
-def _load():
-    global _lib
+def max_threads() -> int:
+    """Host threads the OpenMP build would use (1 without it)."""
+    return int(_load(0).or_threads(0))
+
+
+def _load(threads: int = 1):
+    """The plain library (threads == 1) or the OpenMP one (threads 0 = all host
+    threads, or a count), falling back to the plain one if OpenMP is unavailable."""
+    omp = threads != 1
     with _lock:
-        if _lib is not None:
-            return _lib
-        lib = ctypes.CDLL(build())
+        build()
+        path = _LIB_OMP_PATH if omp and os.path.exists(_LIB_OMP_PATH) else _LIB_PATH
+        lib = _libs.get(path)
+        if lib is not None:
+            if path == _LIB_OMP_PATH:
+                lib.or_threads(threads if threads > 1 else os.cpu_count() or 1)
+            return lib
+        lib = ctypes.CDLL(path)
         sig = {
             "or_create": (_vp, [_i, _i, _pd, _pd, _pi32, _i, _i]),
             "or_destroy": (None, [_vp]),
@@ -88,12 +112,15 @@ def _load():
             "or_dispatch_rates_batch": (None, [_i, _i, _pd, _pi32, _i64, _pu64, _pi32, _pd]),
             "or_sampled_balance": (None, [_i, _i, _pd, _pd, _pi32, _i, _i64, _pu64, _pd, _pd, _d,
                                           _pd, _pd]),
+            "or_threads": (_i, [_i]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
             f.restype = res
             f.argtypes = args
-        _lib = lib
+        _libs[path] = lib
+        if path == _LIB_OMP_PATH:
+            lib.or_threads(threads if threads > 1 else os.cpu_count() or 1)
         return lib
 
 
@@ -115,10 +142,12 @@ def _args(inst=None, **kw):
 
 
 class Oracle:
-    """Handle on the C oracle's state for one instance (keeps the rate table)."""
+    """Handle on the C oracle's state for one instance (keeps the rate table).
+    threads: 1 = the plain single-threaded build; 0 = the OpenMP build on all host
+    threads; k > 1 = the OpenMP build on k threads."""
 
-    def __init__(self, inst=None, **kw):
-        self.lib = _load()
+    def __init__(self, inst=None, threads: int = 1, **kw):
+        self.lib = _load(threads)
         (self.N, self.J, self.lam_j, self.nu, self.pref, self.mode, self.C) = _args(inst, **kw)
         self.ctx = self.lib.or_create(self.N, self.J, _p(self.lam_j, _pd), _p(self.nu, _pd),
                                       _p(self.pref, _pi32), self.mode, self.C)
@@ -249,10 +278,10 @@ class Oracle:
 
 def solve(inst=None, eps: float = 1e-12, delta: float = 1e-20, max_sweeps: int = 100000,
           max_inner: int = 100000, p0=None, sweeps: int | None = None, with_R: bool = True,
-          **kw) -> dict:
+          threads: int = 1, **kw) -> dict:
     """Algorithm 1 to max|p^k - p^{k-1}| <= eps (or exactly ``sweeps`` sweeps), then the
-    birth-death step and the performance measures."""
-    o = Oracle(inst, **kw)
+    birth-death step and the performance measures.  threads as for ``Oracle``."""
+    o = Oracle(inst, threads=threads, **kw)
     try:
         o.build_table()
         o.init(p0)
@@ -269,7 +298,7 @@ def solve(inst=None, eps: float = 1e-12, delta: float = 1e-20, max_sweeps: int =
 
 
 def birth_death(N, mode, C, lam, nu_sum, lam_n, mu_n):
-    lib = _load()
+    lib = _load(1)
     lam_n = np.ascontiguousarray(lam_n, dtype=np.float64)
     mu_n = np.ascontiguousarray(mu_n, dtype=np.float64)
     top = N + C if mode == FINITE else N
@@ -281,14 +310,14 @@ def birth_death(N, mode, C, lam, nu_sum, lam_n, mu_n):
 
 
 def first_idle(pref_row, B: int) -> int:
-    lib = _load()
+    lib = _load(1)
     row = np.ascontiguousarray(pref_row, dtype=np.int32)
     return lib.or_first_idle(len(row), _p(row, _pi32), B)
 
 
 def dispatch_rates(inst=None, src=None, u=None, **kw) -> np.ndarray:
     """lambda_{lm} of Eq. (3) for sampled (source state, unit) pairs."""
-    lib = _load()
+    lib = _load(1)
     N, J, lam_j, nu, pref, mode, C = _args(inst, **kw)
     src = np.ascontiguousarray(src, dtype=np.uint64)
     u = np.ascontiguousarray(u, dtype=np.int32)
@@ -300,7 +329,7 @@ def dispatch_rates(inst=None, src=None, u=None, **kw) -> np.ndarray:
 
 def sampled_balance(inst, B, Pself, Pnb, pq1=0.0):
     """outflow and inflow of Eq. (1) at sampled states, neighbour P given by the caller."""
-    lib = _load()
+    lib = _load(1)
     N, J, lam_j, nu, pref, mode, C = _args(inst)
     B = np.ascontiguousarray(B, dtype=np.uint64)
     Pself = np.ascontiguousarray(Pself, dtype=np.float64)

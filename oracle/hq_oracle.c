@@ -29,6 +29,12 @@
  *     pattern (probability a call from node j is served by unit i), workload,
  *     and the global balance residual of Eq. (1).
  *
+ * Threads: built plainly this file is single-threaded.  Built with -fopenmp, the
+ * loops over the states of one layer (and over states or nodes in the outputs) run
+ * on all host threads, which is the within-layer parallelism of Algorithm 2 (states
+ * of a layer are independent given layers n-1 and n+1); only the order in which the
+ * sums and maxima over a layer are added changes.
+ *
  * Parity pins for this file (tests, CPU only): dense direct solve of Eq. (1)-(2),
  * Erlang-B / M/M/N/N+C / Erlang-C closed forms in the homogeneous case, an N=2
  * hand-derived closed form, the single-unit-first-choice M/M/1/1 marginal, the
@@ -38,6 +44,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define OR_LOSS 0
 #define OR_FINITE 1
@@ -225,6 +234,7 @@ int or_build_up(or_ctx* c, int n_lo, int n_hi) {
     free(c->up[n]);
     c->up[n] = (double*)calloc((size_t)L * N, sizeof(double));
     if (!c->up[n]) return -1;
+#pragma omp parallel for schedule(static)
     for (int64_t k = 0; k < L; k++) {
       uint64_t B = c->lst[c->off[n] + k];
       for (int j = 0; j < c->J; j++) {
@@ -251,6 +261,7 @@ void or_get_up_rows(const or_ctx* c, int n, double* out) {
 void or_layer_rates(or_ctx* c, double* lam_n, double* mu_n) {
   for (int n = 0; n <= c->N; n++) {
     double sl = 0.0, sm = 0.0;
+#pragma omp parallel for schedule(static) reduction(+ : sl, sm)
     for (int64_t k = c->off[n]; k < c->off[n + 1]; k++) {
       uint64_t B = c->lst[k];
       sl += c->p[B] * lambda_m(c, B);
@@ -266,6 +277,7 @@ void or_layer_rates(or_ctx* c, double* lam_n, double* mu_n) {
 void or_init(or_ctx* c, const double* p0) {
   for (int n = 0; n <= c->N; n++) {
     double v = 1.0 / (double)or_layer_size(c, n);
+#pragma omp parallel for schedule(static)
     for (int64_t k = c->off[n]; k < c->off[n + 1]; k++) {
       uint64_t B = c->lst[k];
       c->p[B] = p0 ? p0[B] : v;
@@ -296,6 +308,7 @@ int or_update_layer(or_ctx* c, int n, double delta, int max_inner, double* maxdi
   const uint32_t* st = c->lst + c->off[n];
   double mu_np1 = (n + 1 == N) ? c->nu_sum : c->mu_n[n + 1];
   /* r-independent parts of Eq. (12) */
+#pragma omp parallel for schedule(static)
   for (int64_t k = 0; k < L; k++) {
     uint64_t B = st[k];
     double us = 0.0, ds = 0.0;
@@ -321,6 +334,7 @@ int or_update_layer(or_ctx* c, int n, double delta, int max_inner, double* maxdi
     double mu_prev = c->mu_n[n]; /* mu^{k,r-1}(n) */
     md = 0.0;
     double mu_new = 0.0;
+#pragma omp parallel for schedule(static) reduction(max : md) reduction(+ : mu_new)
     for (int64_t k = 0; k < L; k++) {
       uint64_t B = st[k];
       double denom = lambda_m(c, B) + c->mu_m[B];
@@ -334,6 +348,7 @@ int or_update_layer(or_ctx* c, int n, double delta, int max_inner, double* maxdi
   } while (md > delta && r < max_inner);
   c->inner_total += r;
   double lam_new = 0.0, mx = 0.0, l1 = 0.0;
+#pragma omp parallel for schedule(static) reduction(max : mx) reduction(+ : l1, lam_new)
   for (int64_t k = 0; k < L; k++) {
     uint64_t B = st[k];
     double d = fabs(c->work[k] - c->p[B]);
@@ -425,6 +440,7 @@ void or_birth_death(int N, int mode, int C, double lam, double nu_sum, const dou
 
 /* P{B_m} = p(w(B_m)) * p_{w(B_m)}(B_m)  (Proposition 1) */
 void or_stationary(const or_ctx* c, const double* pn, double* P) {
+#pragma omp parallel for schedule(static)
   for (int64_t y = 0; y < c->S; y++) P[y] = pn[popc((uint64_t)y)] * c->p[y];
 }
 
@@ -443,14 +459,17 @@ double or_outputs(const or_ctx* c, const double* P, double q_busy, double q_wait
   int N = c->N, J = c->J;
   for (int i = 0; i < N; i++) {
     double s = 0.0;
+#pragma omp parallel for schedule(static) reduction(+ : s)
     for (int64_t y = 0; y < c->S; y++)
       if ((y >> i) & 1) s += P[y];
     rho[i] = s + q_busy;
   }
   if (R) {
     for (int64_t k = 0; k < (int64_t)J * N; k++) R[k] = 0.0;
-    for (int64_t y = 0; y < c->S; y++) {
-      for (int j = 0; j < J; j++) {
+    /* node by node (each R[j][.] is added in increasing y, as state by state would) */
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int j = 0; j < J; j++) {
+      for (int64_t y = 0; y < c->S; y++) {
         int u = or_first_idle(N, c->pref + (size_t)j * N, (uint64_t)y);
         if (u >= 0) R[(size_t)j * N + u] += P[y];
       }
@@ -489,6 +508,7 @@ void or_state_balance(const or_ctx* c, const double* P, double pq1, uint64_t B, 
  * construction and are not included). */
 double or_residual(const or_ctx* c, const double* P, double pq1) {
   double mr = 0.0, mo = 0.0;
+#pragma omp parallel for schedule(static) reduction(max : mr, mo)
   for (int64_t y = 0; y < c->S; y++) {
     double o, i;
     or_state_balance(c, P, pq1, (uint64_t)y, &o, &i);
@@ -503,6 +523,17 @@ double or_residual(const or_ctx* c, const double* P, double pq1) {
  * the dispatch rule evaluated on the spot (no stored rates): for very large N,
  * where the full rate table does not fit the test budget.  Pnb[k*N + u] is P of
  * the neighbour of B_k that differs in unit u; Pself[k] = P{B_k}. */
+/* host threads of the OpenMP build (1 in the plain build); n < 1 keeps the default */
+int or_threads(int n) {
+#ifdef _OPENMP
+  if (n >= 1) omp_set_num_threads(n);
+  return omp_get_max_threads();
+#else
+  (void)n;
+  return 1;
+#endif
+}
+
 void or_sampled_balance(int N, int J, const double* lam_j, const double* nu,
                         const int32_t* pref, int mode, int64_t count, const uint64_t* B,
                         const double* Pself, const double* Pnb, double pq1, double* out,
