@@ -85,6 +85,8 @@ def parse():
                     help="one instance load and `--sweeps` sweeps in --precision (fp32, df64, "
                          "fp64, or ir: correction sweeps after 4 FP32 sweeps), nothing else (for ncu)")
     ap.add_argument("--sweeps", type=int, default=2)
+    ap.add_argument("--order", default="ascending", choices=["ascending", "redblack"],
+                    help="sweep order of the solve (--profile and the headline path)")
     return ap.parse_args()
 
 
@@ -105,13 +107,13 @@ def run_profile(args):
         # correction sweeps: a short FP32 solve, then one launch of `sweeps` correction
         # sweeps against an FP64 base of its result (the second k_persist launch)
         rc, st = s.solve(tol=0.0, tol_kind=hq.HQ_TOL_STEP, precision="fp32", max_sweeps=4,
-                         check_every=4)
+                         check_every=4, order=args.order)
         hq.hq_profile_sweep(s.h, hq.HQ_PREC_FP32_IR, args.sweeps)
         st["sweeps_hi"] = args.sweeps
     else:
         prec = args.precision if args.precision in ("fp32", "df64", "fp64") else "df64"
         rc, st = s.solve(tol=0.0, tol_kind=hq.HQ_TOL_STEP, precision=prec, max_sweeps=args.sweeps,
-                         check_every=args.sweeps)
+                         check_every=args.sweeps, order=args.order)
     s.close()
     print(json.dumps({"profile": inst.name, "sweeps": st["sweeps_hi"], "rc": rc}))
     return 0

@@ -77,6 +77,8 @@ typedef enum {
 
 typedef enum { HQ_WARM_NONE = 0, HQ_WARM_GIVEN = 1, HQ_WARM_MLP = 2, HQ_WARM_PRODUCT = 3 } hq_warm;
 
+typedef enum { HQ_ORDER_ASCENDING = 0, HQ_ORDER_REDBLACK = 1 } hq_order;
+
 typedef struct hq_opts {
   double tol;          /* stopping tolerance (see tol_kind) */
   int tol_kind;        /* hq_tol_kind */
@@ -99,7 +101,16 @@ typedef struct hq_opts {
                           observed over the first checks, 90 % of it, at most 1.5,
                           backed off when the steps stop shrinking).  The fixed point
                           is the same for any omega. */
-  int reserved[4];
+  int sweep_order;     /* HQ_ORDER_ASCENDING (0): Algorithm 1's order, layers 1..N-1 in
+                          turn; HQ_ORDER_REDBLACK (1, not in the paper): all odd layers,
+                          then all even layers, each from the other's latest values (the
+                          same fixed point; two grid barriers per sweep instead of N-1) */
+  int debug_barrier;   /* testing only, 0 = off: k > 0 makes CTA k-1 of the first sweep
+                          launch skip its first grid-barrier arrival and every bounded
+                          device wait of that launch give up after 2^20 polls, so the solve
+                          (hq_solve or hq_batch_solve) returns HQ_ETIMEOUT without hanging;
+                          the handle stays usable */
+  int reserved[2];
 } hq_opts;
 
 typedef struct hq_stats {

@@ -63,7 +63,8 @@ static void free_all(hq_solver* h) {
                   h->lidx, h->items, h->wfeat, h->wy, h->wlx,
                   h->b64.T, h->b64.r, h->b64.p, h->b64.nu, h->bdf.T, h->bdf.r, h->bdf.p, h->bdf.nu,
                   h->b32.T, h->b32.r, h->b32.p, h->b32.nu, h->ab, h->partials, h->sc, h->dflag,
-                  h->P, h->pn, h->rho, h->R, h->W, h->summary, h->pcond, h->ir_base, h->ir, h->ir_part};
+                  h->P, h->pn, h->rho, h->R, h->W, h->summary, h->pcond, h->ir_base, h->ir, h->ir_part,
+                  h->wv64, h->wv32, h->sitems[0], h->sitems[1], h->sblocks[0], h->sblocks[1]};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->hsc) cudaFreeHost(h->hsc);
@@ -131,7 +132,8 @@ extern "C" int hq_create(int N, int J, int mode, int capacity_C, void* stream, h
     h->lsize[n] = (int64_t)hq_binom(N, n);
     h->lpad[n] = (h->lsize[n] + 31) & ~(int64_t)31;
     h->off[n + 1] = h->off[n] + h->lpad[n];
-    h->toff[n + 1] = h->toff[n] + (int64_t)n * h->lpad[n];
+    h->tw[n] = HQ_TW(n);
+    h->toff[n + 1] = h->toff[n] + h->tw[n] * h->lpad[n];
     if (h->lpad[n] > h->max_layer) h->max_layer = h->lpad[n];
   }
   for (int n = N + 2; n < HQ_MAXN + 2; n++) {
@@ -165,15 +167,19 @@ extern "C" int hq_create(int N, int J, int mode, int capacity_C, void* stream, h
   HQ_TRY(dalloc(h, (float2**)&h->bdf.p, SP * 8));
   HQ_TRY(dalloc(h, (float**)&h->b32.p, SP * 4));
   HQ_TRY(dalloc(h, &h->ir_base, SP * 8));
-  HQ_TRY(dalloc(h, &h->ir, SP * 24));
+  HQ_TRY(dalloc(h, &h->ir, SP * 12));
+  HQ_TRY(dalloc(h, (double2**)&h->wv64, SP * 16));
+  HQ_TRY(dalloc(h, (float2**)&h->wv32, SP * 8));
   HQ_TRY(dalloc(h, (double**)&h->b64.nu, (int64_t)HQ_MAXN * 8));
   HQ_TRY(dalloc(h, (float2**)&h->bdf.nu, (int64_t)HQ_MAXN * 8));
   HQ_TRY(dalloc(h, (float**)&h->b32.nu, (int64_t)HQ_MAXN * 4));
   // the staging copies of the sweep read up to 15 bytes past a layer's last pair
   h->ab_half_bytes = h->max_layer * 16 + 256;
   HQ_TRY(dalloc(h, (double**)&h->ab, 2 * h->ab_half_bytes));
+  // block partials of the reductions: the sweep kernel's [2][words][grid], the layer
+  // sums' [warps][N+1][4] and the residual's per-block pairs
   int64_t blocks = (h->max_layer + HQ_THREADS - 1) / HQ_THREADS;
-  h->partials_len = blocks * 2 > 152 * 8 * HQ_MAXN ? blocks * 2 : 152 * 8 * HQ_MAXN;
+  h->partials_len = blocks * 2 > ((int64_t)1 << 20) ? blocks * 2 : ((int64_t)1 << 20);
   HQ_TRY(dalloc(h, &h->partials, h->partials_len * 8));
   HQ_TRY(dalloc(h, &h->sc, (int64_t)sizeof(DevScalars)));
   HQ_TRY(dalloc(h, &h->dflag, 16));
@@ -195,10 +201,10 @@ extern "C" int hq_create(int N, int J, int mode, int capacity_C, void* stream, h
   {
     // padding entries are read by the bulk copies: give them defined (zero) contents
     void* zero_bufs[] = {h->masks, h->b64.T, h->b64.r, h->bdf.r, h->b32.r, h->b64.p, h->bdf.p,
-                         h->b32.p, h->ab, h->ir_base, h->ir};
+                         h->b32.p, h->ab, h->ir_base, h->ir, h->wv64, h->wv32};
     int64_t zero_len[] = {SP * 4, TE * 8, SP * 8, SP * 8, SP * 4, SP * 8, SP * 8, SP * 4,
-                          2 * h->ab_half_bytes, SP * 8, SP * 24};
-    for (int i = 0; i < 11 && e == cudaSuccess; i++)
+                          2 * h->ab_half_bytes, SP * 8, SP * 12, SP * 16, SP * 8};
+    for (int i = 0; i < 13 && e == cudaSuccess; i++)
       e = cudaMemsetAsync(zero_bufs[i], 0, (size_t)zero_len[i], h->stream);
   }
   if (e != cudaSuccess) {
@@ -257,6 +263,8 @@ extern "C" int hq_load(hq_solver* h, const double* lambda_j, const double* nu, c
   if (rc != HQ_OK) return rc;
   rc = hq_build_rates(h);
   if (rc != HQ_OK) return rc;
+  rc = hq_build_weights(h);
+  if (rc != HQ_OK) return rc;
   rc = hq_convert_tables(h);
   if (rc != HQ_OK) return rc;
   HQ_CUDA(cudaStreamSynchronize(h->stream));
@@ -285,6 +293,16 @@ extern "C" int hq_solve(hq_solver* h, const hq_opts* opts_in, hq_stats* stats) {
   if (o.warm_start < HQ_WARM_NONE || o.warm_start > HQ_WARM_PRODUCT) { hq_set_error("bad warm_start"); return HQ_EINVAL; }
   if (o.warm_start == HQ_WARM_GIVEN && !o.warm_p) { hq_set_error("warm_p is NULL"); return HQ_EINVAL; }
   if (o.warm_start == HQ_WARM_MLP && !h->mlp) { hq_set_error("no warm-start model is attached"); return HQ_EINVAL; }
+  if (o.sweep_order != HQ_ORDER_ASCENDING && o.sweep_order != HQ_ORDER_REDBLACK) {
+    hq_set_error("sweep_order must be HQ_ORDER_ASCENDING or HQ_ORDER_REDBLACK");
+    return HQ_EINVAL;
+  }
+  if (o.debug_barrier < 0) { hq_set_error("debug_barrier must be >= 0"); return HQ_EINVAL; }
+  h->order = o.sweep_order;
+  // fault injection (tests): CTA debug_barrier - 1 skips its first grid-barrier arrival in
+  // the first sweep launch, and every bounded wait gives up after 2^20 polls
+  h->dbg_skip_cta = o.debug_barrier > 0 ? o.debug_barrier - 1 : -1;
+  h->spin_limit = o.debug_barrier > 0 ? (1u << 20) : 0u;
   // FP32 sweeps stall at their rounding floor; leaving them a check early costs little
   // when the refinement's sweeps cost about as much (correction sweeps), a check late
   // wastes eight sweeps
@@ -359,6 +377,7 @@ extern "C" int hq_solve(hq_solver* h, const hq_opts* opts_in, hq_stats* stats) {
     int nrun = o.check_every;
     if (nrun > o.max_sweeps - total) nrun = o.max_sweeps - total;
     rc = hq_run_sweeps(h, prec, nrun, nullptr, nullptr);
+    h->dbg_skip_cta = -1;
     if (rc != HQ_OK) return rc;
     rc = pull_scalars(h);
     if (rc != HQ_OK) return rc;
@@ -470,6 +489,12 @@ extern "C" int hq_solve(hq_solver* h, const hq_opts* opts_in, hq_stats* stats) {
     prev_check_step = step;
     last_ratio = ratio;
   }
+  h->spin_limit = 0;
+  if (status == HQ_ETIMEOUT) {
+    // the next launch starts from a clean barrier and flag word
+    HQ_CUDA(cudaMemsetAsync(&h->sc->flags, 0, sizeof(int), h->stream));
+    HQ_CUDA(cudaStreamSynchronize(h->stream));
+  }
   if (status == HQ_EDIVERGED || status == HQ_ETIMEOUT) {
     if (stats) {
       memset(stats, 0, sizeof(*stats));
@@ -563,31 +588,63 @@ extern "C" int hq_get_summary(hq_solver* h, double* out5) {
   return copy_out(h, out5, h->summary, 5 * 8, HQ_HOST);
 }
 
+// compact layer-ranked export of the state-major table: entry (n, s, k) of the output
+// (layer n, slot s, rank k) at c_off[n] + s C(N,n) + k
+struct ExportArgs {
+  int N;
+  int64_t off[HQ_MAXN + 2];
+  int64_t toff[HQ_MAXN + 2];
+  int64_t lsize[HQ_MAXN + 1];
+  int64_t tw[HQ_MAXN + 1];
+  int64_t coff[HQ_MAXN + 2];
+};
+
+__global__ void k_table_export(ExportArgs a, int64_t Sp, const double* T, double* out) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= Sp) return;
+  int n = 0;
+  while (n < a.N && a.off[n + 1] <= g) n++;
+  const int64_t k = g - a.off[n];
+  if (n < 1 || k >= a.lsize[n]) return;
+  for (int sl = 0; sl < n; sl++) out[a.coff[n] + sl * a.lsize[n] + k] = T[a.toff[n] + k * a.tw[n] + sl];
+}
+
 extern "C" int hq_get_table(hq_solver* h, double* T, uint32_t* masks, int mem) {
   if (!h) { hq_set_error("NULL solver"); return HQ_EINVAL; }
   if (!h->loaded) { hq_set_error("hq_load has not succeeded"); return HQ_ESTATE; }
-  int rc = HQ_OK;
-  // the device layout pads every layer and table row to 32 entries; hand out the
-  // compact layout described in hq.h
+  if (mem != HQ_HOST && mem != HQ_DEVICE) { hq_set_error("mem must be HQ_HOST or HQ_DEVICE"); return HQ_EINVAL; }
   const cudaMemcpyKind kind = kind_out(mem);
-  int64_t tpos = 0, spos = 0;
-  for (int n = 0; n <= h->N && rc == HQ_OK; n++) {
-    if (T && n >= 1) {
-      cudaError_t e = cudaMemcpy2DAsync((double*)T + tpos, (size_t)h->lsize[n] * 8,
-                                        (const double*)h->b64.T + h->toff[n], (size_t)h->lpad[n] * 8,
-                                        (size_t)h->lsize[n] * 8, (size_t)n, kind, h->stream);
-      if (e != cudaSuccess) rc = hq_cuda_fail(e, "cudaMemcpy2DAsync", __FILE__, __LINE__);
-      tpos += (int64_t)n * h->lsize[n];
+  if (T) {
+    // the device table is state-major and padded; hand out the compact layout of hq.h
+    // (through the transform scratch, which holds exactly N 2^(N-1) doubles, for host output)
+    ExportArgs a;
+    memset(&a, 0, sizeof(a));
+    a.N = h->N;
+    for (int i = 0; i < HQ_MAXN + 2; i++) {
+      a.off[i] = h->off[i];
+      a.toff[i] = h->toff[i];
     }
-    if (masks && rc == HQ_OK) {
-      cudaError_t e = cudaMemcpyAsync(masks + spos, h->masks + h->off[n], (size_t)h->lsize[n] * 4,
-                                      kind, h->stream);
-      if (e != cudaSuccess) rc = hq_cuda_fail(e, "cudaMemcpyAsync", __FILE__, __LINE__);
+    int64_t c = 0;
+    for (int n = 0; n <= h->N; n++) {
+      a.lsize[n] = h->lsize[n];
+      a.tw[n] = h->tw[n];
+      a.coff[n] = c;
+      c += n >= 1 ? (int64_t)n * h->lsize[n] : 0;
+    }
+    double* dst = mem == HQ_DEVICE ? T : h->zeta;
+    k_table_export<<<(unsigned)((h->Sp + 255) / 256), 256, 0, h->stream>>>(a, h->Sp, (const double*)h->b64.T, dst);
+    HQ_LAUNCHED();
+    if (mem == HQ_HOST) HQ_CUDA(cudaMemcpyAsync(T, h->zeta, sizeof(double) * c, cudaMemcpyDeviceToHost, h->stream));
+  }
+  if (masks) {
+    int64_t spos = 0;
+    for (int n = 0; n <= h->N; n++) {
+      HQ_CUDA(cudaMemcpyAsync(masks + spos, h->masks + h->off[n], (size_t)h->lsize[n] * 4, kind, h->stream));
       spos += h->lsize[n];
     }
   }
-  if (rc == HQ_OK) HQ_CUDA(cudaStreamSynchronize(h->stream));
-  return rc;
+  HQ_CUDA(cudaStreamSynchronize(h->stream));
+  return HQ_OK;
 }
 
 extern "C" int hq_get_info(const hq_solver* h, int64_t* out8) {
@@ -607,11 +664,10 @@ extern "C" double hq_sweep_bytes(const hq_solver* h, int precision) {
   if (!h) return 0.0;
   const bool ir = precision == HQ_PREC_FP32_IR;
   const double e = (precision == HQ_PREC_FP32 || ir) ? 4.0 : 8.0;
-  // a correction sweep also reads six FP32 base terms per state (three in the gather,
-  // three in the finalisation)
-  const double extra = ir ? 24.0 : 0.0;
+  // a correction sweep also reads three FP32 base terms per state
+  const double extra = ir ? 12.0 : 0.0;
   double b = 0.0;
-  for (int n = 1; n <= h->N - 1; n++) b += (double)h->lsize[n] * ((n + 3) * e + 4.0 + extra);
+  for (int n = 1; n <= h->N - 1; n++) b += (double)h->lsize[n] * ((n + 3) * e + extra);
   return b;
 }
 

@@ -51,6 +51,7 @@ struct BCfg {
   int64_t toff[HQ_MAXN + 2];
   int64_t lsize[HQ_MAXN + 1];
   int64_t lpad[HQ_MAXN + 1];
+  int64_t tw[HQ_MAXN + 1];
   const uint32_t* masks;
   const uint32_t* lidx;
   const uint32_t* RH;
@@ -82,6 +83,8 @@ struct BatchArgs {
   double* ipart;            // 4 partial sums per item
   unsigned* step_bits;      // [2][K] FP32 bit patterns of the per-sweep step maxima
   unsigned* bar;            // [0] arrivals, [1] (unused), [2] flags
+  unsigned spin_limit;      // polls before a wait gives up (0: the default)
+  int dbg_skip_cta;         // fault injection: this CTA skips its first barrier arrival (-1: none)
 };
 
 template <class V, int kThreads>
@@ -140,12 +143,13 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_batch(BatchArgs a
   auto grid_barrier = [&]() {
     __syncthreads();
     if (threadIdx.x == 0) {
-      red_add_release(&a.bar[0], 1u);
+      if (!(a.dbg_skip_cta == (int)blockIdx.x && gbar == 0)) red_add_release(&a.bar[0], 1u);
       const unsigned target = G * (unsigned)(gbar + 1);
+      const unsigned limit = a.spin_limit ? a.spin_limit : kSpinLimit;
       unsigned it = 0;
       while ((int)(ld_relaxed_u32(&a.bar[0]) - target) < 0) {
         if (*(volatile unsigned*)&a.bar[2] & 2u) break;
-        if (++it > kSpinLimit) {
+        if (++it > limit) {
           atomicOr(&a.bar[2], 2u);
           break;
         }
@@ -199,7 +203,8 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_batch(BatchArgs a
         lv.Sp = C.Sp;
         lv.off_n = C.off[n];
         lv.toff_n = C.toff[n];
-        lv.lp = C.lpad[n];
+        lv.lp = 1;
+        lv.tw = C.tw[n];
         lv.masks = C.masks;
         lv.lidx = C.lidx;
         lv.RH = C.RH;
@@ -502,6 +507,7 @@ extern "C" int hq_batch_create(hq_solver* const* solvers, int count, void* strea
     for (int i = 0; i <= HQ_MAXN; i++) {
       C.lsize[i] = i <= h->N ? h->lsize[i] : 0;
       C.lpad[i] = i <= h->N ? h->lpad[i] : 0;
+      C.tw[i] = i <= h->N ? h->tw[i] : 0;
     }
     C.masks = h->masks;
     C.lidx = h->lidx;
@@ -596,6 +602,7 @@ extern "C" int hq_batch_create(hq_solver* const* solvers, int count, void* strea
   a.ipart = b->ipart;
   a.step_bits = b->step_bits;
   a.bar = b->bar;
+  a.dbg_skip_cta = -1;
   *out = b;
   return HQ_OK;
 }
@@ -700,6 +707,7 @@ extern "C" int hq_batch_solve(hq_batch* b, const hq_opts* opts_in, hq_stats* sta
   if (o.warm_start != HQ_WARM_NONE) { hq_set_error("batched solves start cold"); return HQ_EINVAL; }
   if (o.check_every < 1) o.check_every = 1;
   if (o.precision < HQ_PREC_FP64 || o.precision > HQ_PREC_FP32_FP64) { hq_set_error("bad precision"); return HQ_EINVAL; }
+  if (o.debug_barrier < 0) { hq_set_error("debug_barrier must be >= 0"); return HQ_EINVAL; }
   if (!(o.omega < 2.0) || (o.omega >= 0.0 && o.omega < 1.0 && o.omega != 0.0)) {
     hq_set_error("omega must be 0, in [1, 2), or negative (automatic)");
     return HQ_EINVAL;
@@ -733,7 +741,22 @@ extern "C" int hq_batch_solve(hq_batch* b, const hq_opts* opts_in, hq_stats* sta
     const int prec = phases[ph];
     int nrun = o.check_every;
     if (nrun > o.max_sweeps - total) nrun = o.max_sweeps - total;
-    rc = run_check(b, prec, b->variant[slot_of(prec)], nrun);
+    if (o.debug_barrier > 0 && total == 0) {
+      // fault injection (tests): one direct launch in which CTA debug_barrier - 1 skips its
+      // first grid-barrier arrival and every wait gives up after 2^20 polls; the captured
+      // graph never holds these arguments
+      b->args.dbg_skip_cta = o.debug_barrier - 1;
+      b->args.spin_limit = 1u << 20;
+      rc = record_check(b, prec, b->variant[slot_of(prec)], nrun);
+      if (rc == HQ_OK) {
+        cudaError_t e = cudaStreamSynchronize(b->stream);
+        if (e != cudaSuccess) rc = hq_cuda_fail(e, "batched launch", __FILE__, __LINE__);
+      }
+      b->args.dbg_skip_cta = -1;
+      b->args.spin_limit = 0;
+    } else {
+      rc = run_check(b, prec, b->variant[slot_of(prec)], nrun);
+    }
     if (rc != HQ_OK) return rc;
     total += nrun;
     unsigned flags = 0;

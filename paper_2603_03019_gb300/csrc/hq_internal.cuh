@@ -24,9 +24,20 @@
 // states of one block, processed by one warp: uint4 {rank0, hi | w << 20 | (count-1) << 24,
 // rank of block (hi, w-1) in layer n-1, rank of block (hi, w+1) in layer n+1}.
 #define HQ_ITEM_HI_BITS 20
+// Items of the direct sweep (hq_persist.cu): runs of at most HQ_SW_ITEM consecutive states
+// of one rank block, 8 bytes: x = hi | w << 18 | (count-1) << 22, y = rank of the item's
+// first state in layer n | n << 27.  The sweep takes its high-part neighbour bases, its
+// own block base and its low-part neighbour blocks from RH once per rank block.
+#define HQ_SW_HI_BITS 18
+#define HQ_SW_ITEM 32
 #define HQ_MLP_UNIT_FEATURES 8  // per-unit features of an instance
 #define HQ_MLP_FEATURES 9       // inputs of the warm-start network: unit features + n / N
 #define HQ_MAX_BLOCK 252   // C(HQ_LO_BITS, HQ_LO_BITS / 2)
+// Pull-form table layout: state-major.  The n entries of a state of layer n (busy slot s =
+// s-th busy unit, increasing) are one record of HQ_TW(n) entries (n rounded up to 4, zero
+// padded), so a record starts 16-byte aligned and loads as whole vectors; layer n's
+// records start at toff[n], rank k's at toff[n] + k HQ_TW(n).
+#define HQ_TW(n) (((n) + 3) & ~3)
 
 // ---------------------------------------------------------------------------
 // error plumbing (host)
@@ -180,7 +191,12 @@ struct DevScalars {
   // c1^0(n), c2^0(n) and its per-layer sums {sum mu A0, sum mu B0, sum A0, sum B0}
   double ir_c1[HQ_MAXN + 1];
   double ir_c2[HQ_MAXN + 1];
-  double ir_sum[4][HQ_MAXN + 1];
+  double ir_sum[4][HQ_MAXN + 1];  // the base's layer sums, in the order of ls
+  // the direct sweep's layer sums of the current iterate (FP64): ls[0][n] = sum p,
+  // ls[1][n] = sum mu_m p, ls[2][n] = sum w''(m) p, ls[3][n] = sum v''(m) p, with the
+  // per-state weights w'' (upward) and v'' (downward) of hq_build_weights; correction
+  // sweeps: the full sums of p0 + e (ir_sum holds the base's)
+  double ls[4][HQ_MAXN + 1];
   unsigned long long t_start;  // %globaltimer at the start of the last sweep launch (ns)
   unsigned long long t_phase[64];  // %globaltimer at the release of phase g of that launch
 };
@@ -217,7 +233,8 @@ struct hq_solver {
   int64_t off[HQ_MAXN + 2];    // layer n states start at off[n] (padded to 32 entries)
   int64_t toff[HQ_MAXN + 2];   // table entries of layer n start at toff[n]
   int64_t lsize[HQ_MAXN + 1];  // C(N, n)
-  int64_t lpad[HQ_MAXN + 1];   // C(N, n) rounded up to 32: layer stride, table row stride
+  int64_t lpad[HQ_MAXN + 1];   // C(N, n) rounded up to 32: layer stride
+  int64_t tw[HQ_MAXN + 1];     // table record width of layer n, HQ_TW(n)
   int64_t Sp = 0;              // padded length of the layer-ranked vectors
   int64_t tentries = 0;        // padded table length
   int64_t ab_half_bytes = 0;   // one half of the (A, B) double buffer
@@ -237,8 +254,18 @@ struct hq_solver {
   uint32_t* RL = nullptr;      // 2^L
   uint32_t* RH = nullptr;      // 2^H x (L+1)
   uint32_t* lidx = nullptr;    // 3 x Sp: low-part neighbour positions (4 bytes a word)
-  uint4* items = nullptr;      // work items of the sweep, layer by layer
+  uint4* items = nullptr;      // work items of the batched sweep, layer by layer
   int ifirst[HQ_MAXN + 2];     // items of layer n: [ifirst[n], ifirst[n+1])
+  // direct sweep: items of each sweep order, phase by phase ([order][pfirst[ph], pfirst[ph+1]))
+  uint2* sitems[2] = {nullptr, nullptr};
+  int* sblocks[2] = {nullptr, nullptr};  // first item of each rank block (and the end)
+  int spbfirst[2][HQ_MAXN + 2];  // rank blocks of phase ph: [spbfirst[ph], spbfirst[ph+1])
+  int snph[2] = {0, 0};        // phases per sweep of each order
+  int order = HQ_ORDER_ASCENDING;  // sweep order of the solve in progress
+  unsigned spin_limit = 0;     // bounded waits of the sweep kernel (0: the default)
+  int dbg_skip_cta = -1;       // fault injection: this CTA skips one barrier arrival
+  void* wv64 = nullptr;        // per-state weights (w'', v'') in FP64 (double2, layer-ranked)
+  void* wv32 = nullptr;        // the same in FP32 (float2)
   // instance
   double* lam_j = nullptr;     // J
   double* nu = nullptr;        // N
@@ -267,7 +294,7 @@ struct hq_solver {
   // {rho0, A0, B0, G_rho, G_A, G_B}; the iterate of the correction sweeps is e = p - p0,
   // held in b32.p; ir_part: 4 FP64 partial sums per work item of the base pass
   double* ir_base = nullptr;
-  float* ir = nullptr;
+  float* ir = nullptr;         // 3 x Sp FP32 base terms {rho0, A0, B0} of the correction sweeps
   double* ir_part = nullptr;
   float* wfeat = nullptr;      // N (N-1) rows x HQ_MLP_FEATURES: (layer n, unit i) pairs
   float* wy = nullptr;         // N (N-1) predictions (logit q_i(n))
@@ -296,10 +323,17 @@ int hq_product_warm_start(hq_solver* h, double* P);  // the analytic control (HQ
 #define HQ_PREC_IRC 16
 int hq_ir_begin(hq_solver* h, int from);
 int hq_ir_assemble(hq_solver* h);
+int hq_base_pass(hq_solver* h);  // base scalars c^0 and the FP32 base terms (hq_persist.cu)
 
 // work items and low-part positions of the sweep (hq_items.cu)
 int hq_item_list(int N, std::vector<uint4>& items, int* ifirst);  // host list, layer by layer
+// direct-sweep items of one order, phase by phase, and their rank blocks: block b holds
+// items [blocks[b], blocks[b + 1]); phase ph holds blocks [pbfirst[ph], pbfirst[ph + 1])
+int hq_sweep_item_list(int N, int order, std::vector<uint2>& items, std::vector<int>& blocks, int* pbfirst,
+                       int* nphases);
 int hq_build_items(hq_solver* h);     // at hq_create, after the layout
+int hq_build_weights(hq_solver* h);   // at hq_load, after the table and r (hq_persist.cu)
+int hq_iter_sums(hq_solver* h, int prec, const void* p, double* dst);  // 4 layer sums -> dst[4][N+1] (device)
 int hq_convert_tables(hq_solver* h);  // at hq_load: FP32 and DF64 copies of the table
 
 // table (hq_table.cu)
@@ -308,7 +342,8 @@ int hq_zeta_subset(hq_solver* h, long long* buf, int bits, int count, bool super
 
 // sweep (hq_sweep.cu)
 int hq_init_iterate(hq_solver* h, int prec, const double* warm_y, int warm_mem);
-int hq_convert_iterate(hq_solver* h, int from, int to);
+// sums = false: leave the sweep's layer sums alone (a converted copy for the residual)
+int hq_convert_iterate(hq_solver* h, int from, int to, bool sums = true);
 int hq_run_sweeps(hq_solver* h, int prec, int nsweeps, cudaEvent_t ev0, cudaEvent_t ev1);
 PrecBufs& hq_bufs(hq_solver* h, int prec);
 

@@ -1,7 +1,8 @@
-// Work items of the sweep kernel (built on the host from N alone, at hq_create), the
-// positions of each state's low-part neighbours inside their rank blocks (device, at
-// hq_create), and the FP32 / DF64 copies of the pull-form table (device, at hq_load).
-// The item format is described with HQ_ITEM_HI_BITS in hq_internal.cuh.
+// Work items of the sweep kernels (built on the host from N alone, at hq_create): the
+// direct sweep's per-order lists (format with HQ_SW_HI_BITS) and the batched sweep's
+// list (format with HQ_ITEM_HI_BITS, hq_internal.cuh) with the positions of each
+// state's low-part neighbours inside their rank blocks (device, at hq_create); and the
+// FP32 / DF64 copies of the pull-form table (device, at hq_load).
 #include <vector>
 
 #include "hq_internal.cuh"
@@ -103,7 +104,74 @@ int hq_item_list(int N, std::vector<uint4>& items, int* ifirst) {
   return HQ_OK;
 }
 
+// Items of the direct sweep (format with HQ_SW_HI_BITS in hq_internal.cuh) for one sweep
+// order, phase by phase: HQ_ORDER_ASCENDING has one phase per layer 1..N-1;
+// HQ_ORDER_REDBLACK has the odd layers' items, then the even layers' (one phase if
+// N = 2).  Inside a phase, layers ascend and blocks come in rank order; blocks[] marks
+// where each rank block's items start.
+int hq_sweep_item_list(int N, int order, std::vector<uint2>& items, std::vector<int>& blocks, int* pbfirst,
+                       int* nphases) {
+  static const HostBinom B;
+  const int L = N < HQ_LO_BITS ? N : HQ_LO_BITS, H = N - L;
+  if (H > HQ_SW_HI_BITS) {
+    hq_set_error("item builder: high part too wide");
+    return HQ_EINVAL;
+  }
+  items.clear();
+  blocks.clear();
+  auto add_layer = [&](int n) {
+    for (uint32_t hi = 0; hi < (1u << H); hi++) {
+      const int w = n - __builtin_popcount(hi);
+      if (w < 0 || w > L) continue;
+      const uint64_t start = rank_hi(B, L, hi, w);
+      const int size = (int)B.c[L][w];
+      blocks.push_back((int)items.size());
+      for (int s0 = 0; s0 < size; s0 += HQ_SW_ITEM) {
+        const int c = size - s0 < HQ_SW_ITEM ? size - s0 : HQ_SW_ITEM;
+        items.push_back(make_uint2(hi | ((uint32_t)w << HQ_SW_HI_BITS) | ((uint32_t)(c - 1) << 22),
+                                   (uint32_t)(start + (uint64_t)s0) | ((uint32_t)n << 27)));
+      }
+    }
+  };
+  int np = 0;
+  if (order == HQ_ORDER_ASCENDING) {
+    for (int n = 1; n <= N - 1; n++) {
+      pbfirst[np++] = (int)blocks.size();
+      add_layer(n);
+    }
+  } else {
+    for (int f = 1; f <= 2 && f <= N - 1; f++) {
+      pbfirst[np++] = (int)blocks.size();
+      for (int n = f; n <= N - 1; n += 2) add_layer(n);
+    }
+  }
+  for (int i = np; i < HQ_MAXN + 2; i++) pbfirst[i] = (int)blocks.size();
+  blocks.push_back((int)items.size());
+  *nphases = np;
+  return HQ_OK;
+}
+
 int hq_build_items(hq_solver* h) {
+  for (int order = 0; order < 2; order++) {
+    std::vector<uint2> si;
+    std::vector<int> sb;
+    int rc = hq_sweep_item_list(h->N, order, si, sb, h->spbfirst[order], &h->snph[order]);
+    if (rc != HQ_OK) return rc;
+    const size_t bytes = sizeof(uint2) * (si.empty() ? 1 : si.size());
+    const size_t bbytes = sizeof(int) * sb.size();
+    cudaError_t e = cudaMalloc((void**)&h->sitems[order], bytes);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&h->sblocks[order], bbytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      hq_set_error("cudaMalloc of the sweep items failed");
+      return HQ_ENOMEM;
+    }
+    h->dev_bytes += (int64_t)(bytes + bbytes);
+    if (!si.empty())
+      HQ_CUDA(cudaMemcpyAsync(h->sitems[order], si.data(), bytes, cudaMemcpyHostToDevice, h->stream));
+    HQ_CUDA(cudaMemcpyAsync(h->sblocks[order], sb.data(), bbytes, cudaMemcpyHostToDevice, h->stream));
+    HQ_CUDA(cudaStreamSynchronize(h->stream));  // the host vectors go out of scope
+  }
   std::vector<uint4> items;
   const int rc = hq_item_list(h->N, items, h->ifirst);
   if (rc != HQ_OK) return rc;

@@ -1,49 +1,67 @@
 // Outer iterations k of Algorithm 1 (Eq. 12-14) on the layer-ranked layout, as one
-// persistent kernel per batch of sweeps.
+// persistent cooperative kernel per batch of sweeps.
 //
-// For layer n (ascending: Gauss-Seidel from layer n-1, Jacobi from layer n+1, as in
-// Algorithm 1 and the two properties stated for Algorithm 2) and each state m, Eq. (12)
-// reads
+// The update of layer n.  For each state m of layer n, Eq. (12) reads
 //     p_n^{k,r}(m) = alpha mu^{k,r-1}(n) A_m + beta B_m
 // with  alpha = 1/lambda^k(n-1),  beta = lambda^{k-1}(n) / mu^{k-1}(n+1),
-//       A_m = r_m sum_{l in C_{n-1}} p^k_{n-1}(l) lambda_{lm},
-//       B_m = r_m sum_{u idle in m} p^{k-1}_{n+1}(m+u) nu_u,   r_m = 1/(lambda_m+mu_m).
-// Only mu^{k,r-1}(n) depends on r; with Eq. (14) it obeys mu^{k,r} = a mu^{k,r-1} + b,
-// a = alpha sum_m mu_m A_m in (0,1), b = beta sum_m mu_m B_m, so the inner loop of
-// Algorithm 1 converges to mu* = b/(1-a) and p_n^k(m) = c1 A_m + c2 B_m with
-// c1 = alpha mu*, c2 = beta (the delta -> 0 reading of the inner loop).  Then
-// lambda^k(n) = lambda sum_m p_n^k(m) = lambda (c1 sum A + c2 sum B) (Eq. 13), mu^k(n) = mu*.
+//       A_m = r_m U_m,  U_m = sum_{l in C_{n-1}} p_{n-1}(l) lambda_{lm},
+//       B_m = r_m D_m,  D_m = sum_{u idle in m} p_{n+1}(m+u) nu_u,   r_m = 1/(lambda_m+mu_m).
+// Only mu^{k,r-1}(n) depends on r, and Eq. (14) makes it an affine recursion
+// mu^{k,r} = a mu^{k,r-1} + b with a = alpha sum_m mu_m A_m in (0,1) and
+// b = beta sum_m mu_m B_m, so the inner loop of Algorithm 1 converges to mu* = b/(1-a)
+// and p_n^k(m) = c1 A_m + c2 B_m with c1 = alpha mu*, c2 = beta (its delta -> 0 limit).
 //
-// Schedule.  Phase n of a sweep gathers layer n into (A, B) pairs; c1, c2 of layer n
-// are only known once every CTA has added its share of sum mu_m A_m and sum mu_m B_m.
-// So layer n-1 stays as (A, B) pairs until phase n: the gathers of layer n combine
-// p_{n-1} = c1 A + c2 B on the fly (accumulating sum T A and sum T B separately), and
-// phase n also writes the final p_{n-1} and its step |p^k - p^{k-1}|.  One grid
-// barrier per layer; layer N-1 of sweep k is finalised in phase 1 of sweep k+1 (which
-// does not read it), and a closing phase finalises the last sweep.  Once every CTA has
-// arrived at a barrier, each CTA folds all CTAs' partial sums in the same fixed order
-// and solves the layer's scalar recursion (c1, c2, lambda(n), mu(n), the step) itself:
-// the result is deterministic and identical in every CTA, and no CTA waits for another
-// to publish it.
+// The scalars of layer n come from its neighbour layers, before its gather.  The sums
+// over layer n that the closed form needs are sums over layers n-1 and n+1 with
+// per-state weights that depend on the instance only:
+//     sum_m mu_m A_m = sum_{l in C_{n-1}} p(l) w''(l),   w''(l) = sum_{u idle in l} lambda_u(l) mu_{l+u} r_{l+u},
+//     sum_m mu_m B_m = sum_{l in C_{n+1}} p(l) v''(l),   v''(l) = sum_{u busy in l} nu_u mu_{l-u} r_{l-u},
+// and lambda(n-1) = lambda sum p_{n-1} (Eq. 13), mu(n+1) = sum mu_l p_{n+1}(l) (Eq. 14).
+// So every layer carries four sums {sum p, sum mu p, sum w'' p, sum v'' p}; the phase
+// that writes a layer also adds up its four sums, and the grid barrier that ends the
+// phase folds them, after which every CTA solves the closed form of the layers of the
+// next phase.  The gather then writes the final p_n directly: no (A, B) pairs are
+// stored and no layer is finalised later.
 //
-// Work.  Layer n is cut into items of at most 32 consecutive states of one rank block
-// (see HQ_ITEM_HI_BITS); items go round-robin to the warps of the grid.  A warp first
-// copies the two small blocks that hold its states' neighbours across a low-part unit,
-// (hi, w-1) of the (A, B) pairs of layer n-1 and (hi, w+1) of p of layer n+1, into its
-// own slot of shared memory with coalesced loads, so that the scattered part of the
-// gather reads shared memory; the positions there come precomputed per state (lidx).
-// Neighbours across a high-part unit, and the table rows, are read with coalesced loads
-// straight from global memory: one lane per state, consecutive states at consecutive
-// addresses.  The gather has no per-neighbour branch: the low-part steps are unrolled
-// over the lidx bytes, the high-part ones run over a per-warp list of the item's
-// neighbour blocks, and the low-part table entries are loaded before the staging wait.
-// There is no producer, no stage ring and no wait other than the grid barrier.
+// Sweep orders.  HQ_ORDER_ASCENDING is Algorithm 1 as printed: layers 1..N-1 in turn,
+// Gauss-Seidel from layer n-1, Jacobi from layer n+1 (the two properties stated for
+// Algorithm 2), one phase and one grid barrier per layer.  HQ_ORDER_REDBLACK (not in the
+// paper) updates all odd layers from the even ones, then all even layers from the odd
+// ones: two phases per sweep.  Both are block Gauss-Seidel iterations of the same
+// fixed-point equations, so they share the fixed point (the exact stationary
+// distribution); layer coupling is block tridiagonal, and for such couplings any
+// ordering that updates each layer after one of its neighbours and before the other
+// ("consistent" orderings) has the same asymptotic rate.
 //
-// The grid barrier's wait is bounded: a barrier that does not complete within its
+// Work.  A phase's items (runs of at most 32 consecutive states of one rank block, see
+// HQ_SW_HI_BITS) are split among the warps of the grid in contiguous ranges, so a warp
+// meets the items of one block one after another.  Per block, the warp reads the block
+// bases of its neighbours from RH once (lane j: the block across high unit j; lanes
+// 29..31: its own block and the blocks (hi, w -/+ 1)), and copies the two blocks that hold
+// its states' low-part neighbours -- (hi, w-1) of layer n-1 and (hi, w+1) of layer n+1, at
+// most 252 states each -- into its shared-memory slot with 16-byte asynchronous copies.
+// Per item, every lane (one state) issues all its loads at once before it waits: its n
+// table entries, its high-part neighbours (consecutive states have them at consecutive
+// ranks, so these are coalesced runs), r_m, its old value and its two weights.  State
+// masks and low-part neighbour positions come from shared tables (the low parts of a
+// block in colex order, and RL), not from memory.  The sums keep Algorithm 1's order:
+// busy neighbours by table slot (increasing unit), idle neighbours by unit.
+//
+// Correction sweeps (iterative refinement against an FP64 base p0, FP32): the iterate is
+// e = p - p0, the gathers read e, and the update is
+//     e_n(m) = rho0_m + d1 A0_m + d2 B0_m + c1 a_m + c2 b_m
+// (a, b: the gathers of e; A0, B0, rho0 = c1^0 A0 + c2^0 B0 - p0: per-state base terms in
+// FP32; d = c - c^0), with the layer sums of p0 + e made of the base's (FP64) and the
+// correction's.
+//
+// Every grid barrier's wait is bounded: one that does not complete within its
 // iteration limit sets an error bit in DevScalars::flags and the kernel runs to its end
 // with in-bounds indices; the host reports HQ_ETIMEOUT.
+#include <math.h>
 #include <stdlib.h>
 #include <string.h>
+
+#include <vector>
 
 #include "hq_sweep_dev.cuh"
 
@@ -51,380 +69,828 @@ namespace {
 
 using namespace hqdev;
 
-constexpr int kThreads = 1024;            // 32 warps, one CTA per SM at 64 registers:
-                                          // half the grid arrivals and partials of 2 x 512
-constexpr int kWarps = kThreads / 32;
-constexpr int kPW = 6;                    // partial words per CTA per phase
-constexpr unsigned kSpinLimit = 1u << 24;
+constexpr int kMaxPL = HQ_MAXN / 2;        // layers in one phase, at most (red-black, N = 28)
+constexpr int kMaxWords = 4 * kMaxPL + 1;  // partial words per CTA per phase
+constexpr unsigned kSpinDefault = 1u << 24;
+constexpr unsigned kFull = 0xffffffffu;
 
-struct PersistArgs {
-  int N, L, H, nsweeps;
+// per-state weights (w'', v'') as stored, and as the policy's type
+template <class V> struct WT {
+  typedef double2 W;
+  __device__ static double x(W w) { return w.x; }
+  __device__ static double y(W w) { return w.y; }
+};
+template <> struct WT<PolF32> {
+  typedef float2 W;
+  __device__ static float x(W w) { return w.x; }
+  __device__ static float y(W w) { return w.y; }
+};
+template <> struct WT<PolDF> {
+  typedef double2 W;
+  __device__ static float2 x(W w) { return df_from_double(w.x); }
+  __device__ static float2 y(W w) { return df_from_double(w.y); }
+};
+
+struct SweepArgs {
+  int N, L, H, nsweeps, order, nphases;
   double lam;
-  double omega;                 // over-relaxation of the finalised layers (1: none)
+  double omega;                // over-relaxation of the updated layers (1: none)
   int64_t Sp;
-  int64_t off[HQ_MAXN + 2];     // padded per-state offsets of the layers
-  int64_t toff[HQ_MAXN + 2];    // padded table offsets of the layers
-  int64_t lsize[HQ_MAXN + 1];
-  int64_t lpad[HQ_MAXN + 1];    // table row stride of layer n
-  int ifirst[HQ_MAXN + 2];      // items of layer n: [ifirst[n], ifirst[n+1])
-  const uint4* items;
-  const uint32_t* masks;
-  const uint32_t* lidx;
+  int64_t off[HQ_MAXN + 2];    // padded per-state offsets of the layers
+  int64_t toff[HQ_MAXN + 2];   // padded table offsets of the layers
+  int64_t tw[HQ_MAXN + 2];     // table record width of layer n
+  int pbfirst[HQ_MAXN + 2];    // rank blocks of phase ph: [pbfirst[ph], pbfirst[ph+1])
+  const uint2* items;
+  const int* blocks;           // first item of each rank block (and the end)
   const uint32_t* RL;
   const uint32_t* RH;
   const void* T;
   const void* r;
-  void* p;
+  const void* wv;              // per-state weights (w'', v'')
   const void* nu;
-  void* ab0;
-  void* ab1;
-  double* partials;  // [2][gridDim][kPW]
+  void* p;
+  double* partials;            // [2][kMaxWords][G]
   DevScalars* sc;
-  const float* ir;   // correction sweeps: 6 x Sp base terms {rho0, A0, B0, G_rho, G_A, G_B}
+  const float* ir;             // correction sweeps: 3 x Sp base terms {rho0, A0, B0}
+  float* out;                  // base pass: 3 x Sp {rho0, A0, B0} written (FP32)
+  unsigned spin_limit;
+  int dbg_skip_cta;            // fault injection: this CTA skips its first barrier arrival
 };
 
-template <class V, bool kFullL, bool kIR>
-__global__ void __launch_bounds__(kThreads, 1) k_persist(PersistArgs a) {
-  typedef typename V::T T;
-  typedef Pair<V> PR;
-  typedef typename PR::P P2;
-  // per-warp slots: staged (A, B) block of layer n-1, then staged p block of layer n+1
-  extern __shared__ __align__(128) unsigned char smem[];
-  __shared__ uint32_t s_RL[1 << HQ_LO_BITS];
-  __shared__ int s_binL[HQ_LO_BITS + 2];
-  __shared__ double s_lam[HQ_MAXN + 1], s_mu[HQ_MAXN + 1];
-  __shared__ T s_nu[HQ_MAXN];
-  __shared__ double s_red[kPW][kWarps];
-  __shared__ uint32_t s_hl[kWarps][32];  // per warp: the item's high-part neighbour bases
-  __shared__ T s_hnu[kWarps][32];        // and its idle high-part units' rates
-  __shared__ T s_lamT, s_one;
-  __shared__ T s_c1, s_c2;
-  __shared__ T s_d1, s_d2;  // correction sweeps: c1 - c1^0, c2 - c2^0 of the last layer solved
-  __shared__ double s_step[2];
-  __shared__ double s_alpha, s_beta;  // 1/lambda(n-1) and lambda(n)/mu(n+1) of the layer solved
+// first layer and number of layers of phase ph (red-black: every other layer from f)
+__device__ __forceinline__ void phase_layers(int order, int ph, int N, int& f, int& nl) {
+  f = ph + 1;
+  nl = order == HQ_ORDER_ASCENDING ? 1 : (N - 1 - f) / 2 + 1;
+}
 
-  DevScalars* sc = a.sc;
-  const int N = a.N, L = a.L, H = a.H;
-  const unsigned G = gridDim.x;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  unsigned char* slot_d = smem + (size_t)wid * Slot<V>::kBytes;
-  unsigned char* slot_u = slot_d + Slot<V>::kD;
-  for (int i = threadIdx.x; i < (1 << L); i += blockDim.x) s_RL[i] = a.RL[i];
-  if (threadIdx.x <= L + 1) {
-    // C(L, i - 1): the sizes of the blocks (hi, w -/+ 1) are s_binL[w] and s_binL[w + 2]
-    const int i = threadIdx.x;
-    int c = 0;
-    if (i >= 1) {
-      double v = 1.0;
-      for (int q = 1; q <= i - 1; q++) v = v * (double)(L - (i - 1) + q) / (double)q;
-      c = (int)(v + 0.5);
-    }
-    s_binL[i] = c;
-  }
-  if (threadIdx.x < N) s_nu[threadIdx.x] = ((const T*)a.nu)[threadIdx.x];
-  if (threadIdx.x <= N) {
-    s_lam[threadIdx.x] = sc->lam_n[threadIdx.x];
-    s_mu[threadIdx.x] = sc->mu_n[threadIdx.x];
+// shared tables of one CTA: the low-part tables and per-layer offsets
+template <class V, int kWarps, int kHP>
+struct Smem {
+  typedef typename V::T T;
+  uint32_t RL[1 << HQ_LO_BITS];
+  uint16_t LO[1 << HQ_LO_BITS];     // low parts in colex order, by weight: LO[woff[w] + rank]
+  // per low part (same index as LO), 16 bytes: byte k < w = position RL[lo ^ 2^u] of the
+  // k-th busy unit u's neighbour in block (hi, w-1); byte k >= w = position RL[lo | 2^u]
+  // of the (k-w)-th idle unit u's neighbour in block (hi, w+1); nibble k at bit 80 + 4k
+  // = that idle unit u
+  uint4 LX[1 << HQ_LO_BITS];
+  T MUlo[1 << HQ_LO_BITS];          // sum of nu over the busy units of lo
+  int woff[HQ_LO_BITS + 2];         // woff[w + 1] - woff[w] = C(L, w)
+  T nu[HQ_MAXN];
+  int64_t off[HQ_MAXN + 2], toff[HQ_MAXN + 2], tw[HQ_MAXN + 2];
+  // per warp, for its current rank block: the high-part neighbour runs (busy units in
+  // increasing order, then idle units), and the idle units' rates at the same index
+  const T* hptr[kWarps][kHP];
+  T hnu[kWarps][kHP];
+  double ws[kWarps][kMaxPL][4];     // per warp: layer sums of this phase
+  float wmd[kWarps];
+  double fold[kMaxWords];
+  double LS[4][HQ_MAXN + 1];        // layer sums of the iterate (corrections: p0 + e)
+  double IB[4][HQ_MAXN + 1];        // corrections: the base's layer sums
+  double I1[HQ_MAXN + 1], I2[HQ_MAXN + 1];  // corrections: c1^0, c2^0
+  T c1[HQ_MAXN + 1], c2[HQ_MAXN + 1], d1[HQ_MAXN + 1], d2[HQ_MAXN + 1];
+  double step[2];
+};
+
+template <class V, int kWarps, int kHP>
+__device__ void setup_tables(Smem<V, kWarps, kHP>& s, const SweepArgs& a) {
+  typedef typename V::T T;
+  const int L = a.L, N = a.N;
+  for (int i = threadIdx.x; i < (1 << L); i += blockDim.x) s.RL[i] = a.RL[i];
+  if ((int)threadIdx.x < N) s.nu[threadIdx.x] = ((const T*)a.nu)[threadIdx.x];
+  for (int i = threadIdx.x; i < HQ_MAXN + 2; i += blockDim.x) {
+    s.off[i] = a.off[i];
+    s.toff[i] = a.toff[i];
+    s.tw[i] = a.tw[i];
   }
   if (threadIdx.x == 0) {
-    s_lamT = V::from_d(a.lam);
-    s_one = V::from_d(1.0);
-    s_c1 = V::zero();
-    s_c2 = V::zero();
-    s_d1 = V::zero();
-    s_d2 = V::zero();
-    s_step[0] = s_step[1] = 0.0;
+    s.woff[0] = 0;
+    for (int w = 0; w <= L; w++) {
+      double c = 1.0;  // C(L, w), exact for L <= 10
+      for (int q = 1; q <= w; q++) c = c * (double)(L - w + q) / (double)q;
+      s.woff[w + 1] = s.woff[w] + (int)(c + 0.5);
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < (1 << L); i += blockDim.x) {
+    const uint32_t lo = (uint32_t)i;
+    const int e = s.woff[__popc(lo)] + (int)s.RL[lo];
+    s.LO[e] = (uint16_t)lo;
+    uint32_t wd[4] = {0u, 0u, 0u, 0u};
+    int k = 0;
+    for (int u = 0; u < L; u++)
+      if ((lo >> u) & 1u) {
+        wd[k >> 2] |= (s.RL[lo ^ (1u << u)] & 0xffu) << (8 * (k & 3));
+        k++;
+      }
+    for (int u = 0; u < L; u++)
+      if (!((lo >> u) & 1u)) {
+        wd[k >> 2] |= (s.RL[lo | (1u << u)] & 0xffu) << (8 * (k & 3));
+        const int bit = 80 + 4 * k;
+        wd[bit >> 5] |= (uint32_t)u << (bit & 31);
+        k++;
+      }
+    s.LX[e] = make_uint4(wd[0], wd[1], wd[2], wd[3]);
+    T mu = V::zero();
+    for (uint32_t y = lo; y; y &= y - 1u) mu = V::add(mu, s.nu[__ffs(y) - 1]);
+    s.MUlo[lo] = mu;
+  }
+}
+
+__device__ __forceinline__ uint32_t lx_word(const uint4& x, int i) {
+  return i == 0 ? x.x : (i == 1 ? x.y : (i == 2 ? x.z : x.w));
+}
+
+// A state's table record as loaded: vectors of kPer entries (16 bytes), and entry s of it
+// (s a constant once the caller's loop is unrolled)
+template <class V> struct Vec;
+template <> struct Vec<PolF32> {
+  typedef float4 VT;
+  static constexpr int kPer = 4;
+  __device__ static float get(const float4* v, int s) {
+    const float4 x = v[s >> 2];
+    const int c = s & 3;
+    return c == 0 ? x.x : (c == 1 ? x.y : (c == 2 ? x.z : x.w));
+  }
+};
+template <> struct Vec<PolF64> {
+  typedef double2 VT;
+  static constexpr int kPer = 2;
+  __device__ static double get(const double2* v, int s) { return (s & 1) ? v[s >> 1].y : v[s >> 1].x; }
+};
+template <> struct Vec<PolDF> {
+  typedef float4 VT;
+  static constexpr int kPer = 2;
+  __device__ static float2 get(const float4* v, int s) {
+    return (s & 1) ? make_float2(v[s >> 1].z, v[s >> 1].w) : make_float2(v[s >> 1].x, v[s >> 1].y);
+  }
+};
+__device__ __forceinline__ float4 ld_vec(const float4* p) { return __ldcs(p); }
+__device__ __forceinline__ double2 ld_vec(const double2* p) { return __ldcs(p); }
+
+// Eq. (12)'s two inflow sums of one state whose low part has W busy units: busy
+// neighbours by table slot (low units, then high units: slot W + j), idle neighbours by
+// unit (low, then high).  tv: the state's table record; h: its high-part neighbours (busy
+// units first, as the warp's list); lx: its low-part positions and idle units.
+template <int W, class V, int kHP, int kNV>
+__device__ __forceinline__ void inflows(typename V::T& U, typename V::T& D, const typename Vec<V>::VT* tv,
+                                        const typename V::T* h, const uint4& lx, const typename V::T* sdn,
+                                        const typename V::T* sup, int nbh, int H, int L,
+                                        const typename V::T* nu, const typename V::T* hnu) {
+  constexpr int kMaxSlot = kNV * Vec<V>::kPer;
+#pragma unroll
+  for (int k = 0; k < W; k++) {
+    const uint32_t pos = (lx_word(lx, k >> 2) >> (8 * (k & 3))) & 0xffu;
+    V::fma_acc(U, sdn[pos], Vec<V>::get(tv, k));
+  }
+#pragma unroll
+  for (int j = 0; j < kHP; j++) {
+    if (j >= nbh) break;
+    if (W + j < kMaxSlot) V::fma_acc(U, h[j], Vec<V>::get(tv, W + j));
+  }
+#pragma unroll
+  for (int k = W; k < HQ_LO_BITS; k++) {
+    if (k >= L) break;
+    const uint32_t pos = (lx_word(lx, k >> 2) >> (8 * (k & 3))) & 0xffu;
+    const uint32_t u = (lx_word(lx, (80 + 4 * k) >> 5) >> ((80 + 4 * k) & 31)) & 0xfu;
+    V::fma_acc(D, sup[pos], nu[u]);
+  }
+#pragma unroll
+  for (int j = 0; j < kHP; j++) {
+    if (j >= H) break;
+    if (j < nbh) continue;
+    V::fma_acc(D, h[j], hnu[j]);
+  }
+}
+
+// Process the rank blocks [b0, b1) of a phase whose layers start at f (li = (n - f) >>
+// order), dealt round-robin to the warps of the grid: block b0 + g, b0 + g + nwarps, ...
+// for warp g, so that at any time the warps work on neighbouring blocks (the table and
+// neighbour reads stay within a window of the layer) and each warp stages a block once
+// for all of its items.  One lane per state of an item.
+// kMode 0: a sweep (write p, add the layer sums into s.ws);  kMode 1: a correction
+// sweep (the iterate is e, base terms from a.ir);  kMode 2: the base pass of the
+// refinement (read p = p0, write rho0, A0, B0 to a.out with the scalars c^0 in s.c1/c2;
+// no sums, no update).  md receives the step max |p_new - p_old|.
+// Every per-neighbour loop is unrolled with compile-time indices (registers) and leaves
+// at a warp-uniform bound, so only the neighbours that exist issue instructions.
+template <class V, int kMode, int kHP, int kWarps>
+__device__ __forceinline__ void run_items(Smem<V, kWarps, kHP>& s, const SweepArgs& a, int b0, int b1, int f,
+                                          unsigned char* slot, int kSlot, float& md) {
+  typedef typename V::T T;
+  typedef WT<V> WX;
+  typedef typename WX::W W;
+  typedef typename Vec<V>::VT VT;
+  constexpr int kNV = (kHP + HQ_LO_BITS + Vec<V>::kPer - 1) / Vec<V>::kPer;  // record vectors, at most
+  const int L = a.L, H = a.H, wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const T* pv = (const T*)a.p;
+  T* pw = (T*)a.p;
+  const bool relax = kMode != 2 && a.omega != 1.0;
+  const T om = V::from_d(a.omega);
+  int cur_n = -1, li = 0, nvec = 0;
+  const T *p_dn = nullptr, *p_up = nullptr, *Tn = nullptr, *rn = nullptr;
+  T* p_n = nullptr;
+  const W* wn = nullptr;
+  const float* irn = nullptr;
+  float* outn = nullptr;
+  int64_t tw = 0;
+  T c1 = V::zero(), c2 = V::zero(), d1 = V::zero(), d2 = V::zero();
+  T aS = V::zero(), aM = V::zero(), aW = V::zero(), aV = V::zero();
+  const T* sdn = (const T*)slot;
+  const T* sup = (const T*)(slot + kSlot / 2);
+  auto flush = [&]() {
+    if (kMode == 2) return;
+    T v[4] = {aS, aM, aW, aV};
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      T x = V::norm(v[q]);
+      for (int m = 16; m > 0; m >>= 1) x = V::add(x, V::shfl_xor(x, m));
+      if (lane == 0) s.ws[wid][li][q] += V::to_d(x);
+    }
+  };
+  const int gwarp = (int)blockIdx.x * kWarps + wid, nwarps = (int)gridDim.x * kWarps;
+  for (int blk = b0 + gwarp; blk < b1; blk += nwarps) {
+    const int ib = __ldg(a.blocks + blk), ie = __ldg(a.blocks + blk + 1);
+    const uint2 d0 = __ldg(a.items + ib);
+    const uint32_t hi = d0.x & ((1u << HQ_SW_HI_BITS) - 1u);
+    const int w = (int)((d0.x >> HQ_SW_HI_BITS) & 0xfu);
+    const int n = (int)(d0.y >> 27);
+    if (n != cur_n) {
+      if (cur_n >= 0) flush();
+      cur_n = n;
+      li = (n - f) >> a.order;
+      p_dn = pv + s.off[n - 1];
+      p_up = pv + s.off[n + 1];
+      p_n = pw + s.off[n];
+      Tn = (const T*)a.T + s.toff[n];
+      tw = s.tw[n];
+      nvec = (int)tw / Vec<V>::kPer;
+      rn = (const T*)a.r + s.off[n];
+      wn = (const W*)a.wv + s.off[n];
+      c1 = s.c1[n];
+      c2 = s.c2[n];
+      if constexpr (kMode == 1) {
+        d1 = s.d1[n];
+        d2 = s.d2[n];
+        irn = a.ir + s.off[n];
+      }
+      if constexpr (kMode == 2) outn = a.out + s.off[n];
+      aS = aM = aW = aV = V::zero();
+    }
+    // the block: its neighbour block bases from RH (lane j < H: across high unit L + j;
+    // lanes 29..31: its own block and the blocks (hi, w -/+ 1)), the list of high-part
+    // runs, and the two low-part blocks staged in the warp's slot
+    __syncwarp();  // every lane is done with the previous block's staged values and lists
+    int idx = -1;
+    if (lane < H) idx = (int)((hi ^ (1u << lane)) * (uint32_t)(L + 1)) + w;
+    else if (lane == 29) idx = (int)(hi * (uint32_t)(L + 1)) + w;
+    else if (lane == 30 && w >= 1) idx = (int)(hi * (uint32_t)(L + 1)) + w - 1;
+    else if (lane == 31 && w < L) idx = (int)(hi * (uint32_t)(L + 1)) + w + 1;
+    const uint32_t rh = idx >= 0 ? __ldg(a.RH + idx) : 0u;
+    const int nbh = __popc(hi);
+    T muj = V::zero();
+    if (lane < H) {
+      const int before = __popc(hi & ((1u << lane) - 1u));
+      if ((hi >> lane) & 1u) {
+        s.hptr[wid][before] = p_dn + rh;
+        muj = s.nu[L + lane];
+      } else {
+        const int at = nbh + lane - before;
+        s.hptr[wid][at] = p_up + rh;
+        s.hnu[wid][at] = s.nu[L + lane];
+      }
+    }
+    for (int m = 16; m > 0; m >>= 1) muj = V::add(muj, V::shfl_xor(muj, m));
+    const T mu_hi = muj;
+    const uint32_t hself = __shfl_sync(kFull, rh, 29);
+    {
+      const uint32_t bdn = __shfl_sync(kFull, rh, 30), bup = __shfl_sync(kFull, rh, 31);
+      const int dc = w >= 1 ? s.woff[w] - s.woff[w - 1] : 0;
+      const int uc = w < L ? s.woff[w + 2] - s.woff[w + 1] : 0;
+      const unsigned char* gd = (const unsigned char*)(p_dn + bdn);
+      const unsigned char* gu = (const unsigned char*)(p_up + bup);
+      const int od = (int)((uintptr_t)gd & 15u), ou = (int)((uintptr_t)gu & 15u);
+      const int cd = dc ? (od + dc * (int)sizeof(T) + 15) >> 4 : 0;
+      const int cu = uc ? (ou + uc * (int)sizeof(T) + 15) >> 4 : 0;
+      for (int c = lane; c < cd; c += 32) cp_async16(slot + 16 * c, gd - od + 16 * c);
+      for (int c = lane; c < cu; c += 32) cp_async16(slot + kSlot / 2 + 16 * c, gu - ou + 16 * c);
+      sdn = (const T*)(slot + od);
+      sup = (const T*)(slot + kSlot / 2 + ou);
+    }
+    bool staged = true;
+    __syncwarp();  // the lists are visible to the warp
+    for (int it = ib; it < ie; it++) {
+      const uint2 d = it == ib ? d0 : __ldg(a.items + it);
+      const int cnt = (int)((d.x >> 22) & 0x3fu) + 1;
+      // this lane's state (lanes past the item repeat its first state and discard it)
+      const bool act = lane < cnt;
+      const uint32_t rk = (d.y & ((1u << 27) - 1u)) + (act ? (uint32_t)lane : 0u);
+      const uint32_t rib = rk - hself;
+      // every load of the item before the wait: the table record (vectors), the high-part
+      // neighbours, r, the old value, the weights
+      const VT* rec = (const VT*)(Tn + (int64_t)rk * tw);
+      VT tv[kNV];
+#pragma unroll
+      for (int v = 0; v < kNV; v++) {
+        if (v >= nvec) break;
+        tv[v] = ld_vec(rec + v);
+      }
+      T h[kHP];
+#pragma unroll
+      for (int j = 0; j < kHP; j++) {
+        if (j >= H) break;
+        h[j] = ld_l2(s.hptr[wid][j] + rib);
+      }
+      const T rv = ld_stream(rn + rk);
+      const T po = ld_l2(p_n + rk);
+      W wv = {};
+      if constexpr (kMode != 2) wv = __ldcs(wn + rk);
+      T q0 = V::zero(), q1 = V::zero(), q2 = V::zero();
+      if constexpr (kMode == 1) {
+        q0 = ld_stream(irn + rk);
+        q1 = ld_stream(irn + a.Sp + rk);
+        q2 = ld_stream(irn + 2 * a.Sp + rk);
+      }
+      if (staged) {
+        cp_async_wait_all();
+        __syncwarp();
+        staged = false;
+      }
+      const int ent = s.woff[w] + (int)rib;
+      const uint4 lx = s.LX[ent];
+      T U = V::zero(), D = V::zero();
+      switch (w) {
+#define HQ_INFLOWS(Wc) \
+  case Wc: inflows<Wc, V, kHP, kNV>(U, D, tv, h, lx, sdn, sup, nbh, H, L, s.nu, s.hnu[wid]); break;
+        HQ_INFLOWS(0) HQ_INFLOWS(1) HQ_INFLOWS(2) HQ_INFLOWS(3) HQ_INFLOWS(4) HQ_INFLOWS(5)
+        HQ_INFLOWS(6) HQ_INFLOWS(7) HQ_INFLOWS(8) HQ_INFLOWS(9) HQ_INFLOWS(10)
+#undef HQ_INFLOWS
+        default: break;
+      }
+      U = V::norm(U);
+      D = V::norm(D);
+      const T A = V::mul(U, rv), B = V::mul(D, rv);
+      if constexpr (kMode == 2) {
+        // base pass: rho0 = c1^0 A0 + c2^0 B0 - p0 (FP64 here), stored in FP32
+        if (act) {
+          const double A0 = V::to_d(A), B0 = V::to_d(B);
+          const double rho0 = V::to_d(c1) * A0 + V::to_d(c2) * B0 - V::to_d(po);
+          outn[rk] = (float)rho0;
+          outn[a.Sp + rk] = (float)A0;
+          outn[2 * a.Sp + rk] = (float)B0;
+        }
+      } else {
+        T pn = V::add(V::mul(c1, A), V::mul(c2, B));
+        if constexpr (kMode == 1) pn = V::add(V::add(q0, V::add(V::mul(d1, q1), V::mul(d2, q2))), pn);
+        if (relax) pn = V::add(po, V::mul(om, V::sub(pn, po)));
+        md = fmaxf(md, V::absdiff(pn, po));
+        if (act) {
+          p_n[rk] = pn;
+          aS = V::add(aS, pn);
+          aM = V::add(aM, V::mul(pn, V::add(s.MUlo[s.LO[ent]], mu_hi)));
+          aW = V::add(aW, V::mul(pn, WX::x(wv)));
+          aV = V::add(aV, V::mul(pn, WX::y(wv)));
+        }
+      }
+    }
+  }
+  if (cur_n >= 0) flush();
+}
+
+// closed-form scalars of layer n from the layer sums of its neighbours
+template <class V, int kWarps, int kHP, bool kIR>
+__device__ void solve_layer(Smem<V, kWarps, kHP>& s, const SweepArgs& a, int n) {
+  const double Sd = s.LS[0][n - 1], Wd = s.LS[2][n - 1], Sn = s.LS[0][n];
+  const double Mu = s.LS[1][n + 1], Vu = s.LS[3][n + 1];
+  const double lamd = a.lam * Sd;     // lambda(n-1), Eq. (13)
+  const double alpha = 1.0 / lamd;
+  const double beta = a.lam * Sn / Mu;  // lambda(n) / mu(n+1)
+  const double aa = alpha * Wd;       // alpha sum_m mu_m A_m
+  const double bb = beta * Vu;        // beta sum_m mu_m B_m
+  const double mustar = bb / (1.0 - aa);
+  const double c1 = alpha * mustar;
+  s.c1[n] = V::from_d(c1);
+  s.c2[n] = V::from_d(beta);
+  if (kIR) {
+    s.d1[n] = V::from_d(c1 - s.I1[n]);
+    s.d2[n] = V::from_d(beta - s.I2[n]);
+  }
+  if (blockIdx.x == 0) {
+    a.sc->c1[n] = c1;
+    a.sc->c2[n] = beta;
+    if (!isfinite(mustar) || !(aa < 1.0) || !(c1 >= 0.0)) atomicOr(&a.sc->flags, 1);
+  }
+}
+
+template <class V, bool kIR, int kHP, int kThreads>
+__global__ void __launch_bounds__(kThreads, 1) k_sweep(SweepArgs a) {
+  constexpr int kWarps = kThreads / 32;
+  constexpr int kSlot = 2 * (HQ_MAX_BLOCK * (int)sizeof(typename V::T) + 16);
+  extern __shared__ __align__(128) unsigned char smem_dyn[];
+  __shared__ Smem<V, kWarps, kHP> s;
+  DevScalars* sc = a.sc;
+  const int N = a.N;
+  const unsigned G = gridDim.x;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  unsigned char* slot = smem_dyn + (size_t)wid * kSlot;
+  setup_tables(s, a);
+  for (int i = threadIdx.x; i < 4 * (N + 1); i += kThreads) {
+    const int q = i / (N + 1), n = i % (N + 1);
+    s.LS[q][n] = sc->ls[q][n];
+    if (kIR) s.IB[q][n] = sc->ir_sum[q][n];
+  }
+  if (kIR)
+    for (int n = threadIdx.x; n <= N; n += kThreads) {
+      s.I1[n] = sc->ir_c1[n];
+      s.I2[n] = sc->ir_c2[n];
+    }
+  for (int i = threadIdx.x; i < kWarps * kMaxPL * 4; i += kThreads) (&s.ws[0][0][0])[i] = 0.0;
+  if (threadIdx.x == 0) {
+    s.step[0] = s.step[1] = 0.0;
     if (blockIdx.x == 0) sc->t_start = globaltimer_ns();
   }
   __syncthreads();
-
-  const T* pv = (const T*)a.p;
-  T* pw = (T*)a.p;
-  const T* Tt = (const T*)a.T;
-  const T* rt = (const T*)a.r;
-  const int gwarp = (int)blockIdx.x * kWarps + wid;
-  const int nwarps = (int)G * kWarps;
-  int gphase = 0;  // phase counter within this launch
-
-  // finalise layer lf from the (A, B) buffer `abf`: p = c1 A + c2 B, |p - p_old|; in
-  // correction sweeps e = rho0 + d1 A0 + d2 B0 + c1 a + c2 b (the pairs hold a, b)
-  auto finalize = [&](int lf, const P2* abf, float& md) {
-    const T c1 = s_c1, c2 = s_c2, d1 = s_d1, d2 = s_d2;
-    const bool relax = a.omega != 1.0;
-    const T om = V::from_d(a.omega);
-    T* pl = pw + a.off[lf];
-    const T* r0 = kIR ? (const T*)(a.ir + a.off[lf]) : nullptr;
-    const int64_t Lf = a.lsize[lf];
-    const int64_t nthreads = (int64_t)G * blockDim.x;
-#pragma unroll 4
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < Lf; k += nthreads) {
-      const P2 q = ld_l2(abf + k);
-      const T old = ld_l2(pl + k);
-      T v = V::add(V::mul(c1, PR::A(q)), V::mul(c2, PR::B(q)));
-      if constexpr (kIR) {
-        const T base = V::add(ld_stream(r0 + k),
-                              V::add(V::mul(d1, ld_stream(r0 + a.Sp + k)), V::mul(d2, ld_stream(r0 + 2 * a.Sp + k))));
-        v = V::add(base, v);
-      }
-      if (relax) v = V::add(old, V::mul(om, V::sub(v, old)));
-      md = fmaxf(md, V::absdiff(v, old));
-      pl[k] = v;
-    }
-  };
-
-  // Write this CTA's partials, then the grid barrier.  Arrivals count up on bar_count
-  // (zeroed before the launch, released by the arriving thread so that its partials are
-  // visible); phase g completes when the count reaches G (g + 1).  Then every CTA folds
-  // all partials in CTA order itself -- the same operations in the same order in every
-  // CTA, so all hold the same scalars -- and solves the scalar recursion of layer lg
-  // (if lg > 0).  The two ratios of the closed form that do not depend on this phase's
-  // sums are formed while waiting.  ks: sweep of the layer finalised in this phase (its
-  // step goes into s_step).
-  auto sync_phase = [&](T sA, T sB, T sa, T sb, float md, int lg, int ks) {
-    const int buf = gphase & 1;
-    double* part = a.partials + (size_t)buf * kPW * G;  // [word][CTA]
-    {
-      T w4[4] = {sA, sB, sa, sb};
-#pragma unroll
-      for (int i = 0; i < 4; i++) {
-        const T v = warp_sum<V>(w4[i]);
-        if (lane == 0) s_red[i][wid] = V::to_d(v);
-      }
-      for (int m = 16; m > 0; m >>= 1) md = fmaxf(md, __shfl_xor_sync(0xffffffffu, md, m));
-      if (lane == 0) s_red[4][wid] = (double)md;
-    }
-    __syncthreads();
-    if (wid == 0) {
-      // warp 0 folds the kWarps warp results of each word (few FP64 operations)
-      double v[5];
-#pragma unroll
-      for (int w = 0; w < 5; w++) v[w] = lane < kWarps ? s_red[w][lane] : 0.0;
-#pragma unroll
-      for (int w = 0; w < 5; w++)
-        for (int m = 16; m > 0; m >>= 1) {  // lanes past kWarps hold 0
-          const double o = __shfl_xor_sync(0xffffffffu, v[w], m);
-          v[w] = (w == 4) ? fmax(v[w], o) : v[w] + o;
+  {
+    int f, nl;
+    phase_layers(a.order, 0, N, f, nl);
+    if ((int)threadIdx.x < nl) solve_layer<V, kWarps, kHP, kIR>(s, a, f + ((int)threadIdx.x << a.order));
+  }
+  __syncthreads();
+  const unsigned limit = a.spin_limit ? a.spin_limit : kSpinDefault;
+  int gphase = 0;
+  for (int k = 0; k < a.nsweeps; k++) {
+    if (threadIdx.x == 0) s.step[k & 1] = 0.0;
+    for (int ph = 0; ph < a.nphases; ph++) {
+      int f, nl;
+      phase_layers(a.order, ph, N, f, nl);
+      float md = 0.f;
+      run_items<V, kIR ? 1 : 0, kHP, kWarps>(s, a, a.pbfirst[ph], a.pbfirst[ph + 1], f, slot, kSlot, md);
+      // ---- end of phase: this CTA's partials, the grid barrier, the fold ----------------
+      for (int m = 16; m > 0; m >>= 1) md = fmaxf(md, __shfl_xor_sync(kFull, md, m));
+      if (lane == 0) s.wmd[wid] = md;
+      __syncthreads();
+      const int nw = 4 * nl + 1;
+      double* part = a.partials + (size_t)(gphase & 1) * kMaxWords * G;
+      if ((int)threadIdx.x < nw) {
+        const int t = threadIdx.x;
+        double v = 0.0;
+        if (t < 4 * nl) {
+          const int li = t >> 2, q = t & 3;
+          for (int w2 = 0; w2 < kWarps; w2++) {
+            v += s.ws[w2][li][q];
+            s.ws[w2][li][q] = 0.0;
+          }
+        } else {
+          for (int w2 = 0; w2 < kWarps; w2++) v = fmax(v, (double)s.wmd[w2]);
         }
-      if (lane == 0) {
-        // this thread writes the CTA's partials, so its release covers them
-#pragma unroll
-        for (int w = 0; w < 5; w++) part[(size_t)w * G + blockIdx.x] = v[w];
-        red_add_release(&sc->bar_count, 1u);
-        if (lg > 0) {
-          s_alpha = 1.0 / s_lam[lg - 1];
-          s_beta = s_lam[lg] / s_mu[lg + 1];
-        }
+        part[(size_t)t * G + blockIdx.x] = v;
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        __threadfence();  // the CTA's partials (written before the CTA barrier) go first
+        const bool skip = a.dbg_skip_cta == (int)blockIdx.x && gphase == 0;
+        if (!skip) red_add_release(&sc->bar_count, 1u);
         const unsigned target = G * (unsigned)(gphase + 1);
-        unsigned it = 0;
+        unsigned spins = 0;
         while ((int)(ld_relaxed_u32(&sc->bar_count) - target) < 0) {
-          if (*(volatile int*)&sc->flags & 6) break;  // an earlier wait gave up: do not wait again
-          if (++it > kSpinLimit) {
+          if (*(volatile int*)&sc->flags & 6) break;  // a wait gave up: do not wait again
+          if (++spins > limit) {
             atomicOr(&sc->flags, 2);
             break;
           }
         }
         fence_acq_rel_gpu();
       }
-    }
-    __syncthreads();
-    // fold every CTA's partials in CTA order: warp w < 5 takes word w
-    if (wid < 5) {
-      double v = 0.0;
-      for (unsigned b = lane; b < G; b += 32) {
-        const double x = __ldcg(part + (size_t)wid * G + b);
-        v = (wid == 4) ? fmax(v, x) : v + x;
-      }
-      for (int m = 16; m > 0; m >>= 1) {
-        const double o = __shfl_xor_sync(0xffffffffu, v, m);
-        v = (wid == 4) ? fmax(v, o) : v + o;
-      }
-      if (lane == 0) s_red[wid][0] = v;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double f[5];
-#pragma unroll
-      for (int w = 0; w < 5; w++) f[w] = s_red[w][0];
-      if (kIR && lg > 0) {
-        // the correction sums plus the base's: the sums of the full (A, B) of layer lg
-#pragma unroll
-        for (int w = 0; w < 4; w++) f[w] += sc->ir_sum[w][lg];
-      }
-      if (lg > 0) {
-        // closed-form limit of the inner loop (Eq. 12 and 14), then Eq. (13)
-        const double alpha = s_alpha, beta = s_beta;
-        const double aa = alpha * f[0], bb = beta * f[1];
-        const double mustar = bb / (1.0 - aa);
-        const double c1 = alpha * mustar;
-        s_c1 = V::from_d(c1);
-        s_c2 = V::from_d(beta);
-        if (kIR) {
-          s_d1 = V::from_d(c1 - sc->ir_c1[lg]);
-          s_d2 = V::from_d(beta - sc->ir_c2[lg]);
+      __syncthreads();
+      // every CTA folds every CTA's partials in CTA order: identical scalars everywhere
+      for (int t = wid; t < nw; t += kWarps) {
+        const bool mx = t == 4 * nl;
+        double v = 0.0;
+        for (unsigned c = lane; c < G; c += 32) {
+          const double x = __ldcg(part + (size_t)t * G + c);
+          v = mx ? fmax(v, x) : v + x;
         }
-        s_lam[lg] = a.lam * (c1 * f[2] + beta * f[3]);
-        s_mu[lg] = mustar;
-        if (blockIdx.x == 0) {
-          sc->c1[lg] = c1;
-          sc->c2[lg] = beta;
-          if (!isfinite(mustar) || !(aa < 1.0)) atomicOr(&sc->flags, 1);
+        for (int m = 16; m > 0; m >>= 1) {
+          const double o = __shfl_xor_sync(kFull, v, m);
+          v = mx ? fmax(v, o) : v + o;
         }
+        if (lane == 0) s.fold[t] = v;
       }
-      s_step[ks & 1] = fmax(s_step[ks & 1], f[4]);
-      if (blockIdx.x == 0 && gphase < 64) sc->t_phase[gphase] = globaltimer_ns();
-    }
-    __syncthreads();
-    gphase++;
-  };
-
-  for (int k = 0; k < a.nsweeps; k++) {
-    for (int n = 1; n <= N - 1; n++) {
-      if (threadIdx.x == 0 && n == 1) s_step[k & 1] = 0.0;  // sweep k starts
-      // the layer this phase finalises: gathered in the previous phase (not read in this one)
-      const int fin_layer = gphase == 0 ? -1 : (n == 1 ? N - 1 : n - 1);
-      const P2* ab_prev = (const P2*)(((gphase + 1) & 1) ? a.ab1 : a.ab0);
-      P2* ab_cur = (P2*)((gphase & 1) ? a.ab1 : a.ab0);
-      const T* p_up = pv + a.off[n + 1];
-      float md = 0.f;
-      if (fin_layer > 0) finalize(fin_layer, ab_prev, md);
-      // -- gather layer n -------------------------------------------------------------------
-      T sA = V::zero(), sB = V::zero(), sa = V::zero(), sb = V::zero();
-      LayerView<V> lv;
-      lv.n = n;
-      lv.N = N;
-      lv.L = L;
-      lv.H = H;
-      lv.Sp = a.Sp;
-      lv.off_n = a.off[n];
-      lv.toff_n = a.toff[n];
-      lv.lp = a.lpad[n];
-      lv.masks = a.masks;
-      lv.lidx = a.lidx;
-      lv.RH = a.RH;
-      lv.Tt = Tt;
-      lv.rt = rt;
-      lv.p_up = p_up;
-      lv.ab_prev = ab_prev;
-      lv.ab_cur = ab_cur;
-      lv.nu = s_nu;
-      lv.c1 = s_c1;
-      lv.c2 = s_c2;
-      lv.lamT = s_lamT;
-      lv.one = s_one;
-      lv.gR = kIR ? a.ir + 3 * a.Sp : nullptr;
-      lv.gA = kIR ? a.ir + 4 * a.Sp : nullptr;
-      lv.gB = kIR ? a.ir + 5 * a.Sp : nullptr;
-      lv.d1 = s_d1;
-      lv.d2 = s_d2;
-      const int it_end = a.ifirst[n + 1];
-      int it = a.ifirst[n] + gwarp;
-      uint4 dnext = it < it_end ? __ldg(a.items + it) : make_uint4(0u, 0u, 0u, 0u);
-      for (; it < it_end; it += nwarps) {
-        const uint4 d = dnext;
-        if (it + nwarps < it_end) dnext = __ldg(a.items + it + nwarps);  // next item, ahead
-        gather_item<V, kFullL, kIR>(lv, d, s_RL, s_binL, slot_d, slot_u, s_hl[wid], s_hnu[wid], lane, sA,
-                                    sB, sa, sb);
-        __syncwarp();  // the slot and the lists are rewritten by the next item
+      __syncthreads();
+      if ((int)threadIdx.x < nl) {
+        const int t = threadIdx.x, n = f + (t << a.order);
+#pragma unroll
+        for (int q = 0; q < 4; q++) s.LS[q][n] = s.fold[4 * t + q] + (kIR ? s.IB[q][n] : 0.0);
       }
-      sync_phase(sA, sB, sa, sb, md, n, n >= 2 ? k : k - 1);
+      if (threadIdx.x == 0) {
+        s.step[k & 1] = fmax(s.step[k & 1], s.fold[4 * nl]);
+        if (blockIdx.x == 0 && gphase < 64) sc->t_phase[gphase] = globaltimer_ns();
+      }
+      __syncthreads();
+      {
+        int fn, nln;
+        phase_layers(a.order, ph + 1 < a.nphases ? ph + 1 : 0, N, fn, nln);
+        if ((int)threadIdx.x < nln) solve_layer<V, kWarps, kHP, kIR>(s, a, fn + ((int)threadIdx.x << a.order));
+      }
+      __syncthreads();
+      gphase++;
     }
   }
-  // closing phase: final values of layer N-1 of the last sweep
-  if (gphase > 0) {
-    const int kl = a.nsweeps - 1;
-    float md = 0.f;
-    finalize(N - 1, (const P2*)(((gphase + 1) & 1) ? a.ab1 : a.ab0), md);
-    sync_phase(V::zero(), V::zero(), V::zero(), V::zero(), md, -1, kl);
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-      for (int i = 0; i <= N; i++) {
-        sc->lam_n[i] = s_lam[i];
-        sc->mu_n[i] = s_mu[i];
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    for (int n = 0; n <= N; n++) {
+      for (int q = 0; q < 4; q++) sc->ls[q][n] = s.LS[q][n];
+      if (n < N) {
+        sc->lam_n[n] = a.lam * s.LS[0][n];
+        sc->mu_n[n] = s.LS[1][n];
       }
-      sc->step_prev = a.nsweeps > 1 ? s_step[(kl - 1) & 1] : sc->step;
-      sc->step = s_step[kl & 1];
-      sc->sweeps += a.nsweeps;
-      if (!isfinite(sc->step)) atomicOr(&sc->flags, 1);
     }
+    const int kl = a.nsweeps - 1;
+    sc->step_prev = a.nsweeps > 1 ? s.step[(kl - 1) & 1] : sc->step;
+    sc->step = s.step[kl & 1];
+    sc->sweeps += a.nsweeps;
+    if (!isfinite(sc->step)) atomicOr(&sc->flags, 1);
   }
 }
 
-int g_occ[4][2] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
-int g_nsm = 0;
+// The refinement's base pass: A0, B0 of every state of layers 1..N-1 gathered from p0
+// (FP64 table), rho0 = c1^0 A0 + c2^0 B0 - p0 with c^0 the closed-form scalars of p0's own
+// layer sums (every neighbour taken from p0), written as FP32 base terms.
+template <int kHP, int kThreads>
+__global__ void __launch_bounds__(kThreads, 1) k_base_pass(SweepArgs a) {
+  constexpr int kWarps = kThreads / 32;
+  constexpr int kSlot = 2 * (HQ_MAX_BLOCK * (int)sizeof(double) + 16);
+  extern __shared__ __align__(128) unsigned char smem_dyn[];
+  __shared__ Smem<PolF64, kWarps, kHP> s;
+  const int N = a.N;
+  const int wid = threadIdx.x >> 5;
+  unsigned char* slot = smem_dyn + (size_t)wid * kSlot;
+  setup_tables(s, a);
+  for (int n = threadIdx.x; n <= N; n += kThreads) {
+    s.c1[n] = a.sc->ir_c1[n];
+    s.c2[n] = a.sc->ir_c2[n];
+  }
+  __syncthreads();
+  float md = 0.f;
+  run_items<PolF64, 2, kHP, kWarps>(s, a, a.pbfirst[0], a.pbfirst[a.nphases], 1, slot, kSlot, md);
+}
+
+// base scalars c^0 of every layer from the base's layer sums (Jacobi: all from p0)
+__global__ void k_base_scalars(DevScalars* sc, int N, double lam) {
+  for (int n = 1 + threadIdx.x; n <= N - 1; n += blockDim.x) {
+    const double Sd = sc->ir_sum[0][n - 1], Wd = sc->ir_sum[2][n - 1], Sn = sc->ir_sum[0][n];
+    const double Mu = sc->ir_sum[1][n + 1], Vu = sc->ir_sum[3][n + 1];
+    const double alpha = 1.0 / (lam * Sd), beta = lam * Sn / Mu;
+    const double mustar = beta * Vu / (1.0 - alpha * Wd);
+    sc->ir_c1[n] = alpha * mustar;
+    sc->ir_c2[n] = beta;
+  }
+}
+
+// ---- the four layer sums of an iterate, and the per-state weights ---------------------
+
+// Per warp: a contiguous run of 32-state chunks (layers start on 32-entry boundaries,
+// so a chunk lies in one layer); FP64 sums per layer, written per warp and folded by
+// k_iter_sums_fold in warp order (deterministic).
+struct SumArgs {
+  int N, L;
+  int64_t off[HQ_MAXN + 2];
+  int64_t lsize[HQ_MAXN + 1];
+  const uint32_t* masks;
+  const void* p;
+  const double2* wv;   // FP64 weights
+  const double* nu;
+  double* part;        // [warps][HQ_MAXN + 1][4]
+};
+
+template <class V>
+__global__ void __launch_bounds__(256) k_iter_sums(SumArgs a) {
+  __shared__ double snu[HQ_MAXN];
+  if ((int)threadIdx.x < a.N) snu[threadIdx.x] = a.nu[threadIdx.x];
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int64_t chunks = a.off[a.N + 1] >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t per = (chunks + nw - 1) / nw;
+  const int64_t c0 = gw * per, c1 = c0 + per < chunks ? c0 + per : chunks;
+  double* out = a.part + (size_t)gw * (HQ_MAXN + 1) * 4;
+  for (int i = lane; i < (HQ_MAXN + 1) * 4; i += 32) out[i] = 0.0;
+  __syncwarp();
+  int n = 0;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  const typename V::T* p = (const typename V::T*)a.p;
+  for (int64_t c = c0; c < c1; c++) {
+    const int64_t g = (c << 5) + lane;
+    int nc = n;
+    while (nc < a.N && a.off[nc + 1] <= (c << 5)) nc++;
+    if (nc != n) {
+      for (int q = 0; q < 4; q++) {
+        double v = acc[q];
+        for (int m = 16; m > 0; m >>= 1) v += __shfl_xor_sync(kFull, v, m);
+        if (lane == 0) out[n * 4 + q] += v;
+        acc[q] = 0.0;
+      }
+      n = nc;
+    }
+    if (g - a.off[n] < a.lsize[n]) {
+      const double pv = V::to_d(p[g]);
+      double mu = 0.0;
+      for (uint32_t y = a.masks[g]; y; y &= y - 1u) mu += snu[__ffs(y) - 1];
+      const double2 wq = a.wv[g];
+      acc[0] += pv;
+      acc[1] += pv * mu;
+      acc[2] += pv * wq.x;
+      acc[3] += pv * wq.y;
+    }
+  }
+  for (int q = 0; q < 4; q++) {
+    double v = acc[q];
+    for (int m = 16; m > 0; m >>= 1) v += __shfl_xor_sync(kFull, v, m);
+    if (lane == 0 && c0 < c1) out[n * 4 + q] += v;
+  }
+}
+
+// dst[q][n] = sum over warps (in order) of part[w][n][q]; dst has stride HQ_MAXN + 1
+__global__ void k_iter_sums_fold(int N, int nwarps, const double* part, double* dst) {
+  const int i = threadIdx.x;
+  if (i >= 4 * (N + 1)) return;
+  const int q = i / (N + 1), n = i % (N + 1);
+  double v = 0.0;
+  for (int w = 0; w < nwarps; w++) v += part[((size_t)w * (HQ_MAXN + 1) + n) * 4 + q];
+  dst[q * (HQ_MAXN + 1) + n] = v;
+}
+
+// w''(l) = sum_{u idle in l} lambda_u(l) mu_{l+u} r_{l+u} (the upward rates are the
+// table entries of state l+u at the slot of u), v''(l) = sum_{u busy in l} nu_u mu_{l-u}
+// r_{l-u}, in FP64, and their FP32 copies; padding entries get zeros.
+struct WeightArgs {
+  int N, L;
+  int64_t off[HQ_MAXN + 2];
+  int64_t toff[HQ_MAXN + 2];
+  int64_t lsize[HQ_MAXN + 1];
+  int64_t tw[HQ_MAXN + 1];
+  const uint32_t* masks;
+  const uint32_t* RL;
+  const uint32_t* RH;
+  const double* T;
+  const double* r;
+  const double* nu;
+  double lam, lam_full;
+  double2* w64;
+  float2* w32;
+};
+
+__global__ void __launch_bounds__(256) k_weights(WeightArgs a, int64_t Sp) {
+  __shared__ double snu[HQ_MAXN];
+  if ((int)threadIdx.x < a.N) snu[threadIdx.x] = a.nu[threadIdx.x];
+  __syncthreads();
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= Sp) return;
+  int n = 0;
+  while (n < a.N && a.off[n + 1] <= g) n++;
+  double wu = 0.0, wd = 0.0;
+  if (g - a.off[n] < a.lsize[n]) {
+    const int N = a.N, L = a.L;
+    const uint32_t x = a.masks[g];
+    auto rank = [&](uint32_t y) -> uint32_t {
+      const uint32_t lo = y & ((1u << L) - 1u), hi = y >> L;
+      return __ldg(a.RL + lo) + __ldg(a.RH + (size_t)hi * (L + 1) + __popc(lo));
+    };
+    auto mu_of = [&](uint32_t y) -> double {
+      double m = 0.0;
+      for (; y; y &= y - 1u) m += snu[__ffs(y) - 1];
+      return m;
+    };
+    if (n < N) {
+      for (int u = 0; u < N; u++) {
+        if ((x >> u) & 1u) continue;
+        const uint32_t y = x | (1u << u);
+        const uint32_t ry = rank(y);
+        const int slot = __popc(x & ((1u << u) - 1u));
+        const double t = a.T[a.toff[n + 1] + (int64_t)ry * a.tw[n + 1] + slot];
+        const double ryv = a.r[a.off[n + 1] + ry];
+        wu += t * mu_of(y) * ryv;
+      }
+    }
+    if (n > 0) {
+      for (int u = 0; u < N; u++) {
+        if (!((x >> u) & 1u)) continue;
+        const uint32_t y = x ^ (1u << u);
+        const uint32_t ry = rank(y);
+        wd += snu[u] * mu_of(y) * a.r[a.off[n - 1] + ry];
+      }
+    }
+  }
+  a.w64[g] = make_double2(wu, wd);
+  a.w32[g] = make_float2((float)wu, (float)wd);
+}
+
+// ---- launch ---------------------------------------------------------------------------------
+
+constexpr int kSweepThreads = 512;
+
+// launch-shape experiment (FP32 sweeps, N <= 24): threads per CTA from HQ_SWEEP_THREADS
+int sweep_threads(int H, int kind) {
+  static int t = -1;
+  if (t < 0) {
+    const char* e = getenv("HQ_SWEEP_THREADS");
+    t = e ? atoi(e) : kSweepThreads;
+    if (t != 384 && t != 512 && t != 768 && t != 1024) t = kSweepThreads;
+  }
+  return (H <= 14 && kind == HQ_PREC_FP32) ? t : kSweepThreads;
+}
 
 template <class V, bool kIR>
-const void* persist_fn(bool full) {
-  return full ? (const void*)k_persist<V, true, kIR> : (const void*)k_persist<V, false, kIR>;
+const void* sweep_fn(int H) {
+  if constexpr (V::kind == HQ_PREC_FP32) {
+    if (H <= 14) {
+      switch (sweep_threads(H, V::kind)) {
+        case 384: return (const void*)k_sweep<V, kIR, 14, 384>;
+        case 768: return (const void*)k_sweep<V, kIR, 14, 768>;
+        case 1024: return (const void*)k_sweep<V, kIR, 14, 1024>;
+        default: break;
+      }
+    }
+  }
+  if (H <= 14) return (const void*)k_sweep<V, kIR, 14, kSweepThreads>;
+  return (const void*)k_sweep<V, kIR, 18, kSweepThreads>;
 }
 
-// ir: correction sweeps (FP32 only), against the base set up by hq_ir_begin
-template <class V>
-int launch_persist(hq_solver* h, int nsweeps, cudaEvent_t ev0, cudaEvent_t ev1, bool ir = false) {
-  typedef typename V::T T;
-  typedef typename Pair<V>::P P2;
-  const int slot = ir ? 3 : (V::kind == HQ_PREC_FP64 ? 0 : (V::kind == HQ_PREC_DF64 ? 1 : 2));
-  const size_t smem = (size_t)kWarps * Slot<V>::kBytes;
-  const bool full = h->L == HQ_LO_BITS;
-  const void* kfn = ir ? persist_fn<PolF32, true>(full) : persist_fn<V, false>(full);
-  if (!g_nsm) HQ_CUDA(cudaDeviceGetAttribute(&g_nsm, cudaDevAttrMultiProcessorCount, h->dev));
-  if (!g_occ[slot][full]) {
-    HQ_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  }
-  int occ = 0;
-  HQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kfn, kThreads, smem));
-  if (occ < 1) {
-    hq_set_error("persistent sweep kernel does not fit on an SM");
-    return HQ_ECUDA;
-  }
-  g_occ[slot][full] = occ;
-  const int G = g_nsm * occ;
-  if ((int64_t)G * (nsweeps * (int64_t)(h->N - 1) + 1) >= ((int64_t)1 << 31)) {
-    hq_set_error("too many barrier arrivals for one launch");
-    return HQ_EINVAL;
-  }
-  if ((int64_t)G * kPW * 2 > h->partials_len) {
-    hq_set_error("partials buffer too small for the persistent grid");
-    return HQ_ECUDA;
-  }
-  PrecBufs& b = hq_bufs(h, V::kind);
-  PersistArgs a;
+int g_nsm = 0;
+
+void fill_args(hq_solver* h, SweepArgs& a, int order) {
   memset(&a, 0, sizeof(a));
   a.N = h->N;
   a.L = h->L;
   a.H = h->H;
-  a.nsweeps = nsweeps;
+  a.order = order;
+  a.nphases = h->snph[order];
   a.lam = h->lam;
   a.omega = h->omega;
   a.Sp = h->Sp;
   for (int i = 0; i < HQ_MAXN + 2; i++) {
     a.off[i] = h->off[i];
     a.toff[i] = h->toff[i];
-    a.ifirst[i] = h->ifirst[i];
+    a.tw[i] = i <= h->N ? h->tw[i] : 0;
+    a.pbfirst[i] = h->spbfirst[order][i];
   }
-  for (int n = 0; n <= HQ_MAXN; n++) {
-    a.lsize[n] = n <= h->N ? h->lsize[n] : 0;
-    a.lpad[n] = n <= h->N ? h->lpad[n] : 0;
-  }
-  a.items = h->items;
-  a.masks = h->masks;
-  a.lidx = h->lidx;
+  a.items = h->sitems[order];
+  a.blocks = h->sblocks[order];
   a.RL = h->RL;
   a.RH = h->RH;
-  a.T = b.T;
-  a.r = b.r;
-  a.p = b.p;
-  a.nu = b.nu;
-  a.ab0 = h->ab;
-  a.ab1 = (char*)h->ab + h->ab_half_bytes;
   a.partials = h->partials;
   a.sc = h->sc;
+  a.spin_limit = h->spin_limit;
+  a.dbg_skip_cta = h->dbg_skip_cta;
+}
+
+// ir: correction sweeps (FP32 only), against the base set up by hq_ir_begin
+template <class V>
+int launch_sweep(hq_solver* h, int nsweeps, cudaEvent_t ev0, cudaEvent_t ev1, int G, bool ir) {
+  typedef typename V::T T;
+  const int thr = sweep_threads(h->H, V::kind);
+  const size_t smem = (size_t)(thr / 32) * 2 * (HQ_MAX_BLOCK * sizeof(T) + 16);
+  const void* kfn = ir ? sweep_fn<PolF32, true>(h->H) : sweep_fn<V, false>(h->H);
+  PrecBufs& bp = hq_bufs(h, V::kind);
+  SweepArgs a;
+  fill_args(h, a, h->order);
+  a.nsweeps = nsweeps;
+  a.T = bp.T;
+  a.r = bp.r;
+  a.p = bp.p;
+  a.nu = bp.nu;
+  a.wv = V::kind == HQ_PREC_FP32 ? h->wv32 : h->wv64;
   a.ir = ir ? h->ir : nullptr;
   void* args[] = {&a};
   // a barrier left half-entered by an aborted launch must not leak into this one
   HQ_CUDA(cudaMemsetAsync(&h->sc->bar_count, 0, sizeof(unsigned), h->stream));
   if (ev0) HQ_CUDA(cudaEventRecord(ev0, h->stream));
-  HQ_CUDA(cudaLaunchCooperativeKernel(kfn, dim3(G), dim3(kThreads), args, smem, h->stream));
+  HQ_CUDA(cudaLaunchCooperativeKernel(kfn, dim3(G), dim3(thr), args, smem, h->stream));
   HQ_LAUNCHED();
   if (ev1) HQ_CUDA(cudaEventRecord(ev1, h->stream));
+  return HQ_OK;
+}
+
+// grid of the sweep kernel: one CTA per SM times its occupancy
+template <class V>
+int sweep_grid(hq_solver* h, bool ir, int* G) {
+  typedef typename V::T T;
+  const int thr = sweep_threads(h->H, V::kind);
+  const size_t smem = (size_t)(thr / 32) * 2 * (HQ_MAX_BLOCK * sizeof(T) + 16);
+  const void* kfn = ir ? sweep_fn<PolF32, true>(h->H) : sweep_fn<V, false>(h->H);
+  if (!g_nsm) HQ_CUDA(cudaDeviceGetAttribute(&g_nsm, cudaDevAttrMultiProcessorCount, h->dev));
+  HQ_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int occ = 0;
+  HQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kfn, thr, smem));
+  if (occ < 1) {
+    hq_set_error("persistent sweep kernel does not fit on an SM");
+    return HQ_ECUDA;
+  }
+  *G = g_nsm * occ;
+  if ((int64_t)(*G) * kMaxWords * 2 > h->partials_len) {
+    hq_set_error("partials buffer too small for the persistent grid");
+    return HQ_ECUDA;
+  }
   return HQ_OK;
 }
 
@@ -439,23 +905,106 @@ PrecBufs& hq_bufs(hq_solver* h, int prec) {
 int hq_run_sweeps(hq_solver* h, int prec, int nsweeps, cudaEvent_t ev0, cudaEvent_t ev1) {
   if (h->N < 2 || nsweeps < 1) return HQ_OK;
   h->it_version++;
-  // the barrier's arrival count (grid size x phases of a launch) stays below 2^31
-  const int64_t per = ((int64_t)1 << 31) / ((int64_t)152 * 8 * (h->N - 1) + 1) - 1;
-  // Layer N-1 of a sweep is finalised lazily in phase 1 of the next sweep of the same
-  // launch, whose gather of layer 1 reads layer 2; for N = 3 those are the same layer, so
-  // there every launch runs one sweep (its closing phase finalises layer N-1, and a
-  // launch's first phase finalises nothing)
-  const int cap = h->N == 3 ? 1 : (per > (1 << 20) ? (1 << 20) : (per < 1 ? 1 : (int)per));
+  const bool ir = prec == HQ_PREC_IRC;
+  int G = 0, rc;
+  if (prec == HQ_PREC_FP64) rc = sweep_grid<PolF64>(h, false, &G);
+  else if (prec == HQ_PREC_DF64) rc = sweep_grid<PolDF>(h, false, &G);
+  else rc = sweep_grid<PolF32>(h, ir, &G);
+  if (rc != HQ_OK) return rc;
+  // the barrier's arrival count (grid size x phases of one launch) stays below 2^31
+  const int64_t per = ((int64_t)1 << 31) / ((int64_t)G * h->snph[h->order] + 1) - 1;
+  const int cap = per > (1 << 20) ? (1 << 20) : (per < 1 ? 1 : (int)per);
   for (int done = 0; done < nsweeps;) {
     const int k = nsweeps - done < cap ? nsweeps - done : cap;
     cudaEvent_t e0 = done == 0 ? ev0 : nullptr, e1 = done + k == nsweeps ? ev1 : nullptr;
-    int rc;
-    if (prec == HQ_PREC_FP64) rc = launch_persist<PolF64>(h, k, e0, e1);
-    else if (prec == HQ_PREC_DF64) rc = launch_persist<PolDF>(h, k, e0, e1);
-    else if (prec == HQ_PREC_IRC) rc = launch_persist<PolF32>(h, k, e0, e1, true);
-    else rc = launch_persist<PolF32>(h, k, e0, e1);
+    if (prec == HQ_PREC_FP64) rc = launch_sweep<PolF64>(h, k, e0, e1, G, false);
+    else if (prec == HQ_PREC_DF64) rc = launch_sweep<PolDF>(h, k, e0, e1, G, false);
+    else rc = launch_sweep<PolF32>(h, k, e0, e1, G, ir);
     if (rc != HQ_OK) return rc;
     done += k;
   }
   return HQ_OK;
 }
+
+int hq_base_pass(hq_solver* h) {
+  if (h->N < 2) return HQ_OK;
+  k_base_scalars<<<1, 32, 0, h->stream>>>(h->sc, h->N, h->lam);
+  HQ_LAUNCHED();
+  SweepArgs a;
+  fill_args(h, a, HQ_ORDER_ASCENDING);
+  a.T = h->b64.T;
+  a.r = h->b64.r;
+  a.p = h->ir_base;
+  a.nu = h->b64.nu;
+  a.wv = h->wv64;
+  a.out = h->ir;
+  const size_t smem = (size_t)(kSweepThreads / 32) * 2 * (HQ_MAX_BLOCK * sizeof(double) + 16);
+  const void* kfn = h->H <= 14 ? (const void*)k_base_pass<14, kSweepThreads>
+                               : (const void*)k_base_pass<18, kSweepThreads>;
+  HQ_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  if (!g_nsm) HQ_CUDA(cudaDeviceGetAttribute(&g_nsm, cudaDevAttrMultiProcessorCount, h->dev));
+  void* args[] = {&a};
+  HQ_CUDA(cudaLaunchKernel(kfn, dim3(g_nsm), dim3(kSweepThreads), args, smem, h->stream));
+  HQ_LAUNCHED();
+  return HQ_OK;
+}
+
+int hq_iter_sums(hq_solver* h, int prec, const void* p, double* dst) {
+  SumArgs a;
+  memset(&a, 0, sizeof(a));
+  a.N = h->N;
+  a.L = h->L;
+  for (int i = 0; i < HQ_MAXN + 2; i++) a.off[i] = h->off[i];
+  for (int i = 0; i <= HQ_MAXN; i++) a.lsize[i] = i <= h->N ? h->lsize[i] : 0;
+  a.masks = h->masks;
+  a.p = p;
+  a.wv = (const double2*)h->wv64;
+  a.nu = h->nu;
+  a.part = h->partials;
+  // 8 warps per CTA; at most partials_len / (4 (HQ_MAXN + 1)) warps
+  const int64_t chunks = h->Sp >> 5;
+  int64_t warps = (chunks + 3) / 4;
+  const int64_t wmax = h->partials_len / (4 * (HQ_MAXN + 1));
+  if (warps > wmax) warps = wmax;
+  warps = (warps + 7) / 8 * 8;
+  if (warps > wmax) warps = wmax / 8 * 8;
+  if (warps < 8) warps = 8;
+  const unsigned grid = (unsigned)(warps / 8);
+  if (prec == HQ_PREC_FP64) k_iter_sums<PolF64><<<grid, 256, 0, h->stream>>>(a);
+  else if (prec == HQ_PREC_DF64) k_iter_sums<PolDF><<<grid, 256, 0, h->stream>>>(a);
+  else k_iter_sums<PolF32><<<grid, 256, 0, h->stream>>>(a);
+  HQ_LAUNCHED();
+  k_iter_sums_fold<<<1, 128, 0, h->stream>>>(h->N, (int)warps, h->partials, dst);
+  HQ_LAUNCHED();
+  return HQ_OK;
+}
+
+int hq_build_weights(hq_solver* h) {
+  WeightArgs a;
+  memset(&a, 0, sizeof(a));
+  a.N = h->N;
+  a.L = h->L;
+  for (int i = 0; i < HQ_MAXN + 2; i++) {
+    a.off[i] = h->off[i];
+    a.toff[i] = h->toff[i];
+  }
+  for (int i = 0; i <= HQ_MAXN; i++) {
+    a.lsize[i] = i <= h->N ? h->lsize[i] : 0;
+    a.tw[i] = i <= h->N ? h->tw[i] : 0;
+  }
+  a.masks = h->masks;
+  a.RL = h->RL;
+  a.RH = h->RH;
+  a.T = (const double*)h->b64.T;
+  a.r = (const double*)h->b64.r;
+  a.nu = h->nu;
+  a.lam = h->lam;
+  a.lam_full = h->mode == HQ_LOSS ? 0.0 : h->lam;
+  a.w64 = (double2*)h->wv64;
+  a.w32 = (float2*)h->wv32;
+  k_weights<<<(unsigned)((h->Sp + 255) / 256), 256, 0, h->stream>>>(a, h->Sp);
+  HQ_LAUNCHED();
+  return HQ_OK;
+}
+
+int hq_sweep_partials_words() { return kMaxWords; }

@@ -197,7 +197,7 @@ __global__ void k_birth_death(DevScalars* sc, int N, int mode, int C, double lam
 struct ResArgs {
   int N, L, n, mode;
   int64_t Ln;
-  int64_t Lp;              // table row stride of layer n
+  int64_t tw;              // table record width of layer n
   const uint32_t* masks;   // layer n
   const uint32_t* RL;
   const uint32_t* RH;
@@ -242,7 +242,7 @@ __global__ void __launch_bounds__(256) k_residual(ResArgs a) {
       mu += snu[b];
       uint32_t rk = (b < L) ? s_RL[lo ^ (1u << b)] + __ldg(rh + w - 1)
                             : rl + __ldg(a.RH + (size_t)(hi ^ (1u << (b - L))) * (L + 1) + w);
-      up = fma(__ldg(a.p_dn + rk), __ldcs(a.T + (int64_t)s_ * a.Lp + k), up);
+      up = fma(__ldg(a.p_dn + rk), __ldcs(a.T + k * a.tw + s_), up);
     }
     if (n < a.N) {
       uint32_t full = (1u << a.N) - 1u;
@@ -438,7 +438,7 @@ int hq_layer_sums(hq_solver* h, int prec) {
 static int prepare_fp64(hq_solver* h) {
   if (h->cur_prec != HQ_PREC_FP64) {
     int saved = h->cur_prec;
-    int rc = hq_convert_iterate(h, saved, HQ_PREC_FP64);
+    int rc = hq_convert_iterate(h, saved, HQ_PREC_FP64, false);
     if (rc != HQ_OK) return rc;
     h->cur_prec = saved;  // the iterate still lives in its own precision
   }
@@ -469,7 +469,7 @@ static int residual_pass(hq_solver* h) {
     a.n = n;
     a.mode = h->mode;
     a.Ln = h->lsize[n];
-    a.Lp = h->lpad[n];
+    a.tw = h->tw[n];
     a.masks = h->masks + h->off[n];
     a.RL = h->RL;
     a.RH = h->RH;

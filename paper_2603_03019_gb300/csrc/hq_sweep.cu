@@ -29,7 +29,9 @@ __global__ void k_init_warm(InitArgs a, int64_t Sp, const uint32_t* masks, const
   if (g >= Sp) return;
   int n = 0;
   while (n < a.N && a.off[n + 1] <= g) n++;
-  p[g] = V::from_d(g - a.off[n] < a.lsize[n] ? warm_y[masks[g]] : 0.0);
+  // the empty and the full state are single-state layers: their conditional is 1
+  const double v = (n == 0 || n == a.N) ? 1.0 : warm_y[masks[g]];
+  p[g] = V::from_d(g - a.off[n] < a.lsize[n] ? v : 0.0);
 }
 
 // lambda(n), mu(n) of Eq. (6)-(7) from the layer sums of the current iterate
@@ -84,6 +86,8 @@ int hq_init_iterate(hq_solver* h, int prec, const double* warm_y, int warm_mem) 
   h->cur_prec = prec;
   rc = hq_layer_sums(h, prec);
   if (rc != HQ_OK) return rc;
+  rc = hq_iter_sums(h, prec, hq_bufs(h, prec).p, &h->sc->ls[0][0]);
+  if (rc != HQ_OK) return rc;
   HQ_CUDA(cudaMemsetAsync(&h->sc->sweeps, 0, sizeof(int), h->stream));
   k_set_layer_rates<<<1, 32, 0, h->stream>>>(h->sc, h->N, h->lam,
                                              h->mode == HQ_LOSS ? 0.0 : h->lam, h->nu_sum);
@@ -105,7 +109,7 @@ __global__ void k_f32_to_df(int64_t S, const float* src, float2* dst) {
   dst[g] = make_float2(src[g], 0.f);
 }
 
-int hq_convert_iterate(hq_solver* h, int from, int to) {
+int hq_convert_iterate(hq_solver* h, int from, int to, bool sums) {
   if (from == to) return HQ_OK;
   h->it_version++;
   if (to == HQ_PREC_IRC) return hq_ir_begin(h, from);
@@ -114,7 +118,7 @@ int hq_convert_iterate(hq_solver* h, int from, int to) {
     const int rc = hq_ir_assemble(h);
     if (rc != HQ_OK) return rc;
     h->cur_prec = HQ_PREC_FP64;
-    if (to == HQ_PREC_FP64) return HQ_OK;
+    if (to == HQ_PREC_FP64) return sums ? hq_iter_sums(h, HQ_PREC_FP64, h->b64.p, &h->sc->ls[0][0]) : HQ_OK;
     from = HQ_PREC_FP64;
   }
   const int64_t S = h->Sp;
@@ -135,5 +139,6 @@ int hq_convert_iterate(hq_solver* h, int from, int to) {
     k_convert<PolF64, PolF32><<<grid, 256, 0, h->stream>>>(S, (const double*)s, (float*)d);
   HQ_LAUNCHED();
   h->cur_prec = to;
-  return HQ_OK;
+  // the sweep reads the layer sums of the iterate in its new precision
+  return sums ? hq_iter_sums(h, to, d, &h->sc->ls[0][0]) : HQ_OK;
 }

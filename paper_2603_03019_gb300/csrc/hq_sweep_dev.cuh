@@ -98,7 +98,8 @@ template <class V> struct LayerView {
   int64_t Sp;       // padded state count (row stride of lidx)
   int64_t off_n;    // first state of layer n in the layer-ranked vectors
   int64_t toff_n;   // first table entry of layer n
-  int64_t lp;       // table row stride of layer n
+  int64_t lp;       // distance between a state's consecutive table slots (1: state-major)
+  int64_t tw;       // table record width of layer n
   const uint32_t* masks;
   const uint32_t* lidx;
   const uint32_t* RH;
@@ -181,7 +182,7 @@ __device__ __forceinline__ void gather_item(const LayerView<V>& lv, const uint4 
       g2 = ld_stream(lv.gB + gi);
     }
   }
-  const T* tcol = lv.Tt + lv.toff_n + kq;  // table slot s at tcol[s * lp]
+  const T* tcol = lv.Tt + lv.toff_n + (int64_t)kq * lv.tw;  // table slot s at tcol[s * lp]
   const int64_t lp = lv.lp;
   // table entries of the low-part busy neighbours, issued before the staging wait
   T tlo[HQ_LO_BITS];

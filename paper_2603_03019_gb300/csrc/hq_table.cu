@@ -16,7 +16,7 @@
 // so the quantum is ~2^-62 lambda) and every sum after that is an integer add, which
 // also keeps the transform off GB300's slow FP64 pipe.  The emit converts to FP64 in
 // the pull layout (FP32 and double-float copies follow from it)
-//     T[toff(n) + s C(N,n) + k] = F_{c_s}(m_k - c_s),
+//     T[toff(n) + k HQ_TW(n) + s] = F_{c_s}(m_k - c_s),
 // m_k the rank-k state of layer n and c_s its s-th busy unit, so the sweep reads
 // slot s of consecutive states contiguously.
 #include "hq_internal.cuh"
@@ -39,25 +39,18 @@ __global__ void k_prefix_masks(int N, int J, const int32_t* pref, uint32_t* pre)
   }
 }
 
-// g_u histogram: one CTA per unit u.  Each node j whose key is new (no lower
-// j' shares it) sums its group's rates, each quantised as round(lambda_j scale) with
-// scale a power of two, so the result does not depend on thread timing.
+// g_u histograms: one thread per (node j, unit u) adds round(lambda_j scale) (scale a
+// power of two) to F_u[pre_j(u) without bit u].  The adds are integer atomics, so the
+// sums are exact and do not depend on their order: O(J N) work, deterministic.
 __global__ void k_histogram(int N, int J, const uint32_t* pre, const double* lam_j, double scale,
                             long long* zeta) {
-  int u = blockIdx.x;
-  int64_t half = (int64_t)1 << (N - 1);
-  long long* F = zeta + (int64_t)u * half;
-  for (int j = threadIdx.x; j < J; j += blockDim.x) {
-    uint32_t key = squeeze_bit(__ldg(pre + (int64_t)j * N + u), u);
-    bool leader = true;
-    for (int jp = 0; jp < j && leader; jp++)
-      if (squeeze_bit(__ldg(pre + (int64_t)jp * N + u), u) == key) leader = false;
-    if (!leader) continue;
-    long long s = 0;
-    for (int jp = j; jp < J; jp++)
-      if (squeeze_bit(__ldg(pre + (int64_t)jp * N + u), u) == key) s += __double2ll_rn(__ldg(lam_j + jp) * scale);
-    F[key] = s;
-  }
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= (int64_t)J * N) return;
+  const int j = (int)(g / N), u = (int)(g % N);
+  const int64_t half = (int64_t)1 << (N - 1);
+  const uint32_t key = squeeze_bit(__ldg(pre + g), u);
+  const long long q = __double2ll_rn(__ldg(lam_j + j) * scale);
+  if (q) atomicAdd((unsigned long long*)(zeta + (int64_t)u * half + key), (unsigned long long)q);
 }
 
 // ---------------------------------------------------------------------------
@@ -174,7 +167,7 @@ struct EmitArgs {
   int64_t off[HQ_MAXN + 2];   // padded layer starts
   int64_t toff[HQ_MAXN + 2];  // padded table layer starts
   int64_t lsize[HQ_MAXN + 1];
-  int64_t lpad[HQ_MAXN + 1];  // row stride
+  int64_t tw[HQ_MAXN + 1];    // record width (state-major layout, HQ_TW)
 };
 
 // one thread per state of layers 1..N: slot s <- F_{c_s}(m - c_s) / scale
@@ -186,13 +179,13 @@ __global__ void k_emit(EmitArgs a, int64_t S, const uint32_t* masks, const long 
   while (n < a.N && a.off[n + 1] <= g) n++;
   int64_t k = g - a.off[n];
   if (k >= a.lsize[n]) return;  // padding
-  int64_t Ln = a.lpad[n];
+  const int64_t rec = a.toff[n] + k * a.tw[n];
   int64_t half = (int64_t)1 << (a.N - 1);
   uint32_t x = masks[g];
   int s = 0;
   for (uint32_t y = x; y; y &= y - 1, s++) {
     int u = __ffs(y) - 1;
-    T64[a.toff[n] + (int64_t)s * Ln + k] = (double)__ldg(zeta + (int64_t)u * half + squeeze_bit(x, u)) * inv_scale;
+    T64[rec + s] = (double)__ldg(zeta + (int64_t)u * half + squeeze_bit(x, u)) * inv_scale;
   }
 }
 
@@ -208,7 +201,7 @@ int hq_build_table(hq_solver* h) {
   const double scale = ldexp(1.0, e);  // exact powers of two: the scaling is exact
   long long* z = (long long*)h->zeta;
   HQ_CUDA(cudaMemsetAsync(z, 0, sizeof(long long) * half * N, h->stream));
-  k_histogram<<<N, 256, 0, h->stream>>>(N, J, h->pre, h->lam_j, scale, z);
+  k_histogram<<<(unsigned)(((int64_t)J * N + 255) / 256), 256, 0, h->stream>>>(N, J, h->pre, h->lam_j, scale, z);
   HQ_LAUNCHED();
   int rc = hq_zeta_subset(h, z, N - 1, N, false);
   if (rc != HQ_OK) return rc;
@@ -220,7 +213,7 @@ int hq_build_table(hq_solver* h) {
   }
   for (int i = 0; i <= HQ_MAXN; i++) {
     a.lsize[i] = i <= N ? h->lsize[i] : 0;
-    a.lpad[i] = i <= N ? h->lpad[i] : 0;
+    a.tw[i] = i <= N ? h->tw[i] : 0;
   }
   int64_t cnt = h->Sp - h->off[1];
   k_emit<<<(unsigned)((cnt + 255) / 256), 256, 0, h->stream>>>(

@@ -22,6 +22,8 @@ HQ_HOST, HQ_DEVICE = 0, 1
 HQ_PREC_FP64, HQ_PREC_DF64, HQ_PREC_FP32, HQ_PREC_FP32_DF64, HQ_PREC_FP32_FP64, HQ_PREC_FP32_IR = 0, 1, 2, 3, 4, 5
 HQ_TOL_STEP, HQ_TOL_RESIDUAL = 0, 1
 HQ_WARM_NONE, HQ_WARM_GIVEN, HQ_WARM_MLP, HQ_WARM_PRODUCT = 0, 1, 2, 3
+HQ_ORDER_ASCENDING, HQ_ORDER_REDBLACK = 0, 1
+ORDER = {"ascending": HQ_ORDER_ASCENDING, "redblack": HQ_ORDER_REDBLACK}
 
 PRECISION = {"fp64": HQ_PREC_FP64, "df64": HQ_PREC_DF64, "fp32": HQ_PREC_FP32,
              "fp32+df64": HQ_PREC_FP32_DF64, "fp32+fp64": HQ_PREC_FP32_FP64, "fp32+ir": HQ_PREC_FP32_IR}
@@ -32,7 +34,8 @@ class hq_opts(ctypes.Structure):
                 ("precision", ctypes.c_int), ("check_every", ctypes.c_int),
                 ("warm_start", ctypes.c_int), ("warm_mem", ctypes.c_int),
                 ("warm_p", ctypes.c_void_p), ("fp32_stall", ctypes.c_double),
-                ("omega", ctypes.c_double), ("reserved", ctypes.c_int * 4)]
+                ("omega", ctypes.c_double), ("sweep_order", ctypes.c_int),
+                ("debug_barrier", ctypes.c_int), ("reserved", ctypes.c_int * 2)]
 
 
 class hq_stats(ctypes.Structure):
@@ -242,7 +245,21 @@ def hq_sweep_bytes(h: int, precision: int) -> float:
 
 
 def hq_dispatch_table_static(N: int, J: int, lambda_j, pref, T, stream=None) -> None:
-    """Upward-rate table without any device allocation (all arguments device tensors)."""
+    """Upward-rate table without any device allocation.  lambda_j (J float64), pref (J x N
+    int32) and T (at least N 2^(N-1) float64) are contiguous CUDA tensors on the current
+    device; the C side cannot check pointers, so the binding does."""
+    import torch
+
+    dev = torch.cuda.current_device()
+    for name, t, dt, count in (("lambda_j", lambda_j, torch.float64, J),
+                               ("pref", pref, torch.int32, J * N),
+                               ("T", T, torch.float64, N << (N - 1) if N >= 1 else 0)):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.device.index == dev):
+            raise ValueError(f"{name} must be a CUDA tensor on the current device (cuda:{dev})")
+        if t.dtype != dt or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous {dt} tensor")
+        if t.numel() < count:
+            raise ValueError(f"{name} holds {t.numel()} elements, {count} needed")
     s = stream if isinstance(stream, int) or stream is None else stream.cuda_stream
     _check(load().hq_dispatch_table_static(N, J, lambda_j.data_ptr(), pref.data_ptr(),
                                            T.data_ptr(), s))
@@ -408,8 +425,10 @@ class Solver:
 
     def solve(self, tol=1e-10, tol_kind=HQ_TOL_RESIDUAL, precision="fp32+df64", max_sweeps=100000,
               check_every=8, warm_p=None, fp32_stall=0.0, warm_mlp=False, warm_product=False,
-              omega=1.0) -> tuple[int, dict]:
+              omega=1.0, order="ascending", debug_barrier=0) -> tuple[int, dict]:
         o = hq_default_opts()
+        o.sweep_order = ORDER[order] if isinstance(order, str) else int(order)
+        o.debug_barrier = debug_barrier
         o.tol = tol
         o.tol_kind = tol_kind
         o.precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
