@@ -5,8 +5,10 @@
 // which can synchronise the whole device, is not acceptable.
 //
 // The caller passes the instance (device memory) and the output table (device
-// memory).  The working memory of the transform -- the per-unit subset-sum
-// buffers, the preference-prefix masks and an error word -- lives in one
+// memory).  The arithmetic is the regular load's: every lambda_j is quantised to 64-bit
+// fixed point at the same power-of-two scale and summed by integer adds, so the table is
+// bitwise the one hq_load builds.  The working memory of the transform -- the per-unit
+// subset-sum buffers, the preference-prefix masks, an error word and the scale -- lives in one
 // file-scope device array of fixed size, so this file never calls cudaMalloc,
 // cudaFree or any allocating library routine.  Limits: N <= 16 units,
 // J <= 4096 nodes (4.25 MiB of static device memory, held by every device that
@@ -25,7 +27,7 @@
 // layout of the array (units of 8 bytes):
 //   [0, 16 * 2^15)                     subset-sum buffers, unit u at u * 2^(N-1)
 //   next HQ_STATIC_MAX_J * 16 / 2      prefix masks (uint32, J x N)
-//   next 32                            error word and padding
+//   next 32                            error word, the fixed-point scale and its inverse
 #define HQ_STATIC_ZETA_WORDS ((size_t)HQ_STATIC_MAX_N << (HQ_STATIC_MAX_N - 1))
 #define HQ_STATIC_PRE_WORDS ((size_t)HQ_STATIC_MAX_J * HQ_STATIC_MAX_N / 2)
 #define HQ_STATIC_WORDS (HQ_STATIC_ZETA_WORDS + HQ_STATIC_PRE_WORDS + 32)
@@ -66,38 +68,53 @@ __global__ void k_st_check_rates(int J, const double* lam_j, int* flag) {
   if (!(v >= 0.0) || isinf(v)) atomicOr(flag, 2);
 }
 
-// per-unit histogram of lambda_j over the prefix sets, in increasing j per key
-__global__ void k_st_hist(int N, int J, const uint32_t* pre, const double* lam_j, double* zeta) {
-  const int u = blockIdx.x;
-  double* F = zeta + ((int64_t)u << (N - 1));
-  for (int j = threadIdx.x; j < J; j += blockDim.x) {
-    const uint32_t key = st_squeeze(pre[(int64_t)j * N + u], u);
-    bool first = true;
-    for (int q = 0; q < j && first; q++)
-      if (st_squeeze(pre[(int64_t)q * N + u], u) == key) first = false;
-    if (!first) continue;
-    double s = 0.0;
-    for (int q = j; q < J; q++)
-      if (st_squeeze(pre[(int64_t)q * N + u], u) == key) s += lam_j[q];
-    F[key] = s;
+// lambda = sum_j lambda_j in the order the regular load uses (1024 threads, strided
+// partials, then a halving tree), and from it the same power-of-two fixed-point scale
+// 2^(61 - e), lambda < 2^e, so that both builds quantise every rate identically
+__global__ void k_st_scale(int J, const double* lam_j, double* scale2) {
+  __shared__ double s[1024];
+  double acc = 0.0;
+  for (int j = threadIdx.x; j < J; j += blockDim.x) acc += lam_j[j];
+  s[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) s[threadIdx.x] += s[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    int ex = 0;
+    frexp(s[0] > 0.0 ? s[0] : 1.0, &ex);
+    scale2[0] = ldexp(1.0, 61 - ex);
+    scale2[1] = ldexp(1.0, ex - 61);
   }
 }
 
-// one bit of the subset-sum transform over all N buffers
-__global__ void k_st_zeta_bit(int N, int b, double* zeta) {
+// per-unit histograms in 64-bit fixed point: exact integer adds, order-free
+__global__ void k_st_hist(int N, int J, const uint32_t* pre, const double* lam_j, const double* scale2,
+                          long long* zeta) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= (int64_t)J * N) return;
+  const int j = (int)(g / N), u = (int)(g % N);
+  const uint32_t key = st_squeeze(pre[g], u);
+  const long long q = __double2ll_rn(lam_j[j] * scale2[0]);
+  if (q) atomicAdd((unsigned long long*)(zeta + ((int64_t)u << (N - 1)) + key), (unsigned long long)q);
+}
+
+// one bit of the subset-sum transform over all N buffers (integer adds)
+__global__ void k_st_zeta_bit(int N, int b, long long* zeta) {
   const int64_t half = (int64_t)1 << (N - 1);
   const int64_t pairs = (half >> 1) * N;
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < pairs;
        q += (int64_t)gridDim.x * blockDim.x) {
     const int64_t u = q / (half >> 1), r = q % (half >> 1);
     const int64_t lo = ((r >> b) << (b + 1)) | (r & ((1ll << b) - 1));
-    double* F = zeta + u * half;
+    long long* F = zeta + u * half;
     F[lo | (1ll << b)] += F[lo];
   }
 }
 
 // pull-form emit with an on-the-fly colex unrank (no mask buffer)
-__global__ void k_st_emit(int N, const double* zeta, double* T) {
+__global__ void k_st_emit(int N, const long long* zeta, const double* scale2, double* T) {
   __shared__ uint32_t bc[HQ_STATIC_MAX_N + 1][HQ_STATIC_MAX_N + 2];
   for (int i = threadIdx.x; i < (HQ_STATIC_MAX_N + 1) * (HQ_STATIC_MAX_N + 2); i += blockDim.x) {
     int a = i / (HQ_STATIC_MAX_N + 2), k = i % (HQ_STATIC_MAX_N + 2);
@@ -135,7 +152,7 @@ __global__ void k_st_emit(int N, const double* zeta, double* T) {
     int s = 0;
     for (uint32_t y = x; y; y &= y - 1, s++) {
       const int u = __ffs(y) - 1;
-      T[toff + (int64_t)s * Ln + rank] = zeta[(int64_t)u * half + st_squeeze(x, u)];
+      T[toff + (int64_t)s * Ln + rank] = (double)zeta[(int64_t)u * half + st_squeeze(x, u)] * scale2[1];
     }
   }
 }
@@ -179,18 +196,21 @@ extern "C" int hq_dispatch_table_static(int N, int J, const double* lambda_j, co
   int rc = static_scratch(&base);
   if (rc != HQ_OK) return rc;
   cudaStream_t st = (cudaStream_t)stream;
-  double* zeta = base;
+  long long* zeta = (long long*)base;
   uint32_t* pre = (uint32_t*)(base + HQ_STATIC_ZETA_WORDS);
   int* flag = (int*)(base + HQ_STATIC_ZETA_WORDS + HQ_STATIC_PRE_WORDS);
+  double* scale2 = base + HQ_STATIC_ZETA_WORDS + HQ_STATIC_PRE_WORDS + 2;
   const int64_t half = (int64_t)1 << (N - 1);
   // what must start at zero: the error word and the N subset-sum buffers
   HQ_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), st));
-  HQ_CUDA(cudaMemsetAsync(zeta, 0, sizeof(double) * half * N, st));
+  HQ_CUDA(cudaMemsetAsync(zeta, 0, sizeof(long long) * half * N, st));
   k_st_prefix<<<(J + 127) / 128, 128, 0, st>>>(N, J, pref, pre, flag);
   HQ_LAUNCHED();
   k_st_check_rates<<<(J + 127) / 128, 128, 0, st>>>(J, lambda_j, flag);
   HQ_LAUNCHED();
-  k_st_hist<<<N, 256, 0, st>>>(N, J, pre, lambda_j, zeta);
+  k_st_scale<<<1, 1024, 0, st>>>(J, lambda_j, scale2);
+  HQ_LAUNCHED();
+  k_st_hist<<<(unsigned)(((int64_t)J * N + 255) / 256), 256, 0, st>>>(N, J, pre, lambda_j, scale2, zeta);
   HQ_LAUNCHED();
   for (int b = 0; b + 1 < N; b++) {
     int64_t pairs = (half >> 1) * N;
@@ -200,7 +220,7 @@ extern "C" int hq_dispatch_table_static(int N, int J, const double* lambda_j, co
   }
   const int64_t states = ((int64_t)1 << N) - 1;
   unsigned grid = (unsigned)((states + 255) / 256 < 2048 ? (states + 255) / 256 : 2048);
-  k_st_emit<<<grid, 256, 0, st>>>(N, zeta, T);
+  k_st_emit<<<grid, 256, 0, st>>>(N, zeta, scale2, T);
   HQ_LAUNCHED();
   int host_flag = 0;
   HQ_CUDA(cudaMemcpyAsync(&host_flag, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
