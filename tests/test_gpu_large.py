@@ -1,0 +1,118 @@
+"""The benchmark's solve path against the oracle at full size (N=24) and at N=20.
+
+N=24, J=1000, infinite queue, load 0.8 (the benchmark workload): the oracle's solution
+is stored in tests/golden/inf_n24_j1000_s3001.npz (written by make_large_golden.py from
+the oracle alone: Algorithm 1 to a step of 1e-15, residual 2.4e-16).  The GPU solves
+with the benchmark's options -- FP32 sweeps then FP32 correction sweeps against an FP64
+base, automatic over-relaxation -- in Algorithm 1's order and in red-black order.
+
+Tolerances.  The target is 1e-10 max-abs on P, p(n), rho, R and W.  A solve stopped at
+the benchmark's 1e-10 relative balance residual leaves an error of about the residual
+times the chain's relaxation factor in the largest probabilities (about 8e-10 in P and
+1e-8 relative in p(n) here: the all-busy state and the queue hold a few per cent of the
+mass), so at that tolerance the stated bound for this reduced-precision form is 5e-9
+max-abs; the same path run to a 1e-12 residual meets 1e-10 everywhere.
+
+N=20, J=500, loss system, loads 0.3 / 0.6 / 0.9: full oracle solves in the test (the
+oracle's OpenMP build), compared element by element with both refinement forms.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2603_03019_gb300 import hq
+from paper_2603_03019_gb300 import instances as I
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "inf_n24_j1000_s3001.npz")
+
+
+@pytest.fixture(scope="module")
+def golden():
+    g = np.load(GOLDEN)
+    return {k: g[k] for k in g.files}
+
+
+@pytest.fixture(scope="module")
+def n24():
+    inst = I.large_infinite_n24(3001)
+    s = hq.Solver.for_instance(inst)
+    yield inst, s
+    s.close()
+
+
+def _compare_n24(s, inst, g, tol_abs):
+    P = s.stationary()
+    pn, tail = s.layer_marginals()
+    rho, R, W = s.utilisation(), s.response_pattern(), s.workload()
+    y = g["y"].astype(np.int64)
+    err = {"P": float(np.max(np.abs(P[y] - g["P"]))),
+           "pn": float(np.max(np.abs(pn - g["pn"]))),
+           "tail": abs(tail - float(g["queue_tail"])),
+           "rho": float(np.max(np.abs(rho - g["rho"]))),
+           "R": float(np.max(np.abs(R - g["R"]))),
+           "W": float(np.max(np.abs(W - g["W"])))}
+    for k, v in err.items():
+        assert v <= tol_abs, (k, v, err)
+    return err
+
+
+@pytest.mark.parametrize("order", ["ascending", "redblack"])
+def test_n24_bench_path_against_golden(gpu_lib, golden, n24, order):
+    """The benchmark's exact solve (1e-10 residual), then the same path to 1e-12."""
+    inst, s = n24
+    assert golden["name"] == inst.name
+    rc, st = s.solve(tol=1e-10, precision="fp32+ir", omega=-1.0, check_every=8, order=order)
+    assert rc == hq.HQ_OK and st["final_residual"] <= 1e-10, st
+    assert st["ir_bases"] >= 1 and st["sweeps_fp32"] > 0 and st["sweeps_hi"] > 0
+    _compare_n24(s, inst, golden, 5e-9)
+    rc, st = s.solve(tol=1e-12, precision="fp32+ir", omega=-1.0, check_every=8, order=order)
+    assert rc == hq.HQ_OK and st["final_residual"] <= 1e-12, st
+    _compare_n24(s, inst, golden, 1e-10)
+
+
+def test_n24_plain_fp64_against_golden(gpu_lib, golden, n24):
+    """Algorithm 1 as printed (FP64, no relaxation).  Its slowest mode is smooth across
+    the states and shows little in the balance residual: at 1e-12 it still leaves a
+    relative error of ~1e-9 in P, which rho (a sum over 2^23 states) shows as 9e-10; at
+    1e-13 every output is within 1e-10."""
+    inst, s = n24
+    rc, st = s.solve(tol=1e-13, precision="fp64", omega=1.0, check_every=8)
+    assert rc == hq.HQ_OK, st
+    _compare_n24(s, inst, golden, 1e-10)
+
+
+@pytest.fixture(scope="module")
+def n20_oracle():
+    cache = {}
+
+    def get(load):
+        if load not in cache:
+            inst = I.mixed_n20(2001, load)
+            cache[load] = (inst, oracle.solve(inst, eps=1e-15, threads=0))
+        return cache[load]
+    return get
+
+
+@pytest.mark.parametrize("order", ["ascending", "redblack"])
+@pytest.mark.parametrize("prec", ["fp32+ir", "fp32+df64"])
+@pytest.mark.parametrize("load", [0.3, 0.6, 0.9])
+def test_n20_loads_against_oracle(gpu_lib, n20_oracle, load, prec, order):
+    inst, r = n20_oracle(load)
+    s = hq.Solver.for_instance(inst)
+    rc, st = s.solve(tol=1e-12, precision=prec, omega=-1.0, order=order)
+    assert rc == hq.HQ_OK, st
+    P, rho, R, W = s.stationary(), s.utilisation(), s.response_pattern(), s.workload()
+    pn, _ = s.layer_marginals()
+    summ = s.summary()
+    s.close()
+    assert np.max(np.abs(P - r["P"])) < 1e-10
+    assert np.max(np.abs(pn - r["pn"])) < 1e-10
+    assert np.max(np.abs(rho - r["rho"])) < 1e-10
+    assert np.max(np.abs(R - r["R"])) < 1e-10
+    assert np.max(np.abs(W - r["W"])) < 1e-10
+    assert abs(summ["throughput"] - r["throughput"]) < 1e-10
+    assert summ["residual"] <= 1e-12

@@ -233,7 +233,7 @@ def test_mixed_n20_against_oracle(gpu_lib):
     inst = I.mixed_n20(2001, 0.6)
     g = _solve_gpu(inst, tol=1e-13, precision="fp32+df64")
     assert g["rc"] == hq.HQ_OK
-    r = oracle.solve(inst, eps=1e-15)
+    r = oracle.solve(inst, eps=1e-15, threads=0)
     assert np.max(np.abs(g["P"] - r["P"])) < 1e-10
     assert np.max(np.abs(g["pn"] - r["pn"])) < 1e-10
     assert np.max(np.abs(g["rho"] - r["rho"])) < 1e-10
@@ -348,7 +348,7 @@ def test_refinement_matches_fp64_and_rebases(gpu_lib):
     assert rc == hq.HQ_OK, st2
     assert st2["sweeps_fp32"] == 16 and 2 <= st2["ir_bases"] <= 4
     assert np.max(np.abs(s.stationary() - P64)) < 1e-11
-    r = oracle.solve(inst, eps=1e-15)
+    r = oracle.solve(inst, eps=1e-15, threads=0)
     assert np.max(np.abs(P64 - r["P"])) < 1e-10
     ms = hq.hq_profile_sweep(s.h, hq.HQ_PREC_FP32_IR, 2)
     assert ms > 0
