@@ -64,7 +64,8 @@ static void free_all(hq_solver* h) {
                   h->b64.T, h->b64.r, h->b64.p, h->b64.nu, h->bdf.T, h->bdf.r, h->bdf.p, h->bdf.nu,
                   h->b32.T, h->b32.r, h->b32.p, h->b32.nu, h->ab, h->partials, h->sc, h->dflag,
                   h->P, h->pn, h->rho, h->R, h->W, h->summary, h->pcond, h->ir_base, h->ir, h->ir_part,
-                  h->wv64, h->wv32, h->sitems[0], h->sitems[1], h->sblocks[0], h->sblocks[1]};
+                  h->wv64, h->wv32, h->sitems[0], h->sitems[1], h->sblocks[0], h->sblocks[1],
+                  h->sperm[0], h->sperm[1]};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->hsc) cudaFreeHost(h->hsc);

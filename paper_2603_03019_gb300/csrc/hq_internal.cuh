@@ -259,6 +259,7 @@ struct hq_solver {
   // direct sweep: items of each sweep order, phase by phase ([order][pfirst[ph], pfirst[ph+1]))
   uint2* sitems[2] = {nullptr, nullptr};
   int* sblocks[2] = {nullptr, nullptr};  // first item of each rank block (and the end)
+  int* sperm[2] = {nullptr, nullptr};    // per phase, its blocks by decreasing cost
   int spbfirst[2][HQ_MAXN + 2];  // rank blocks of phase ph: [spbfirst[ph], spbfirst[ph+1])
   int snph[2] = {0, 0};        // phases per sweep of each order
   int order = HQ_ORDER_ASCENDING;  // sweep order of the solve in progress

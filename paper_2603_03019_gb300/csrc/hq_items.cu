@@ -3,6 +3,7 @@
 // list (format with HQ_ITEM_HI_BITS, hq_internal.cuh) with the positions of each
 // state's low-part neighbours inside their rank blocks (device, at hq_create); and the
 // FP32 / DF64 copies of the pull-form table (device, at hq_load).
+#include <algorithm>
 #include <vector>
 
 #include "hq_internal.cuh"
@@ -151,25 +152,49 @@ int hq_sweep_item_list(int N, int order, std::vector<uint2>& items, std::vector<
   return HQ_OK;
 }
 
+// Per phase, its rank blocks by decreasing cost (ties by index): the sweep deals them to
+// the warps in snake order (round r goes warp 0..W-1 when r is even, W-1..0 when odd), which
+// evens out the warps' totals.  A block's cost counts, per item, the loads of a lane
+// (table record, all N neighbours, a few per-state values) plus a fixed set-up per block.
+void hq_block_order(int N, const std::vector<uint2>& items, const std::vector<int>& blocks, const int* pbfirst,
+                    int nphases, std::vector<int>& perm) {
+  perm.resize(blocks.size() > 0 ? blocks.size() - 1 : 0);
+  std::vector<double> cost(perm.size());
+  for (size_t b = 0; b < perm.size(); b++) {
+    const int ni = blocks[b + 1] - blocks[b];
+    const int n = (int)(items[blocks[b]].y >> 27);
+    cost[b] = 24.0 + (double)ni * (HQ_TW(n) + N + 8);
+    perm[b] = (int)b;
+  }
+  for (int ph = 0; ph < nphases; ph++)
+    std::stable_sort(perm.begin() + pbfirst[ph], perm.begin() + pbfirst[ph + 1],
+                     [&](int x, int y) { return cost[x] > cost[y]; });
+}
+
 int hq_build_items(hq_solver* h) {
   for (int order = 0; order < 2; order++) {
     std::vector<uint2> si;
-    std::vector<int> sb;
+    std::vector<int> sb, perm;
     int rc = hq_sweep_item_list(h->N, order, si, sb, h->spbfirst[order], &h->snph[order]);
     if (rc != HQ_OK) return rc;
+    hq_block_order(h->N, si, sb, h->spbfirst[order], h->snph[order], perm);
     const size_t bytes = sizeof(uint2) * (si.empty() ? 1 : si.size());
     const size_t bbytes = sizeof(int) * sb.size();
+    const size_t pbytes = sizeof(int) * (perm.empty() ? 1 : perm.size());
     cudaError_t e = cudaMalloc((void**)&h->sitems[order], bytes);
     if (e == cudaSuccess) e = cudaMalloc((void**)&h->sblocks[order], bbytes);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&h->sperm[order], pbytes);
     if (e != cudaSuccess) {
       cudaGetLastError();
       hq_set_error("cudaMalloc of the sweep items failed");
       return HQ_ENOMEM;
     }
-    h->dev_bytes += (int64_t)(bytes + bbytes);
+    h->dev_bytes += (int64_t)(bytes + bbytes + pbytes);
     if (!si.empty())
       HQ_CUDA(cudaMemcpyAsync(h->sitems[order], si.data(), bytes, cudaMemcpyHostToDevice, h->stream));
     HQ_CUDA(cudaMemcpyAsync(h->sblocks[order], sb.data(), bbytes, cudaMemcpyHostToDevice, h->stream));
+    if (!perm.empty())
+      HQ_CUDA(cudaMemcpyAsync(h->sperm[order], perm.data(), pbytes, cudaMemcpyHostToDevice, h->stream));
     HQ_CUDA(cudaStreamSynchronize(h->stream));  // the host vectors go out of scope
   }
   std::vector<uint4> items;

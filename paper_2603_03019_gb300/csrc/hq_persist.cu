@@ -33,19 +33,23 @@
 // ordering that updates each layer after one of its neighbours and before the other
 // ("consistent" orderings) has the same asymptotic rate.
 //
-// Work.  A phase's items (runs of at most 32 consecutive states of one rank block, see
-// HQ_SW_HI_BITS) are split among the warps of the grid in contiguous ranges, so a warp
-// meets the items of one block one after another.  Per block, the warp reads the block
-// bases of its neighbours from RH once (lane j: the block across high unit j; lanes
-// 29..31: its own block and the blocks (hi, w -/+ 1)), and copies the two blocks that hold
-// its states' low-part neighbours -- (hi, w-1) of layer n-1 and (hi, w+1) of layer n+1, at
-// most 252 states each -- into its shared-memory slot with 16-byte asynchronous copies.
-// Per item, every lane (one state) issues all its loads at once before it waits: its n
-// table entries, its high-part neighbours (consecutive states have them at consecutive
-// ranks, so these are coalesced runs), r_m, its old value and its two weights.  State
-// masks and low-part neighbour positions come from shared tables (the low parts of a
-// block in colex order, and RL), not from memory.  The sums keep Algorithm 1's order:
-// busy neighbours by table slot (increasing unit), idle neighbours by unit.
+// Work.  The pull-form table is state-major: a state's n upward rates form one record,
+// padded to a multiple of four entries, which a lane loads as 16-byte vectors.  A phase's
+// rank blocks (the states of one layer sharing their high part, see HQ_SW_HI_BITS) are
+// sorted by cost and dealt to the warps of the grid in snake order, which evens out the
+// warps' totals; a block's items (runs of at most 32 consecutive states) go to one warp,
+// one lane per state.  Per block, the warp reads its neighbour block bases from RH once
+// (lane j: the block across high unit j; lanes 29..31: its own block and the blocks
+// (hi, w -/+ 1)), lists its high-part neighbour runs in shared memory, and copies the two
+// blocks that hold its states' low-part neighbours -- (hi, w-1) of layer n-1 and (hi, w+1)
+// of layer n+1, at most 252 states each -- into its shared-memory slot with 16-byte
+// asynchronous copies.  Per item, every lane issues all its loads at once before it
+// waits: its table record, its high-part neighbours (consecutive states have them at
+// consecutive ranks, so these are coalesced runs), r_m, its old value and its two weights.
+// Low-part neighbour positions and idle units come from a shared table per low part, so
+// no index is read from memory.  The inflow sums are unrolled per low-part weight w, so
+// every register index is a constant; busy neighbours go by table slot (increasing
+// unit), idle neighbours by unit, the low and the high part as two chains added at the end.
 //
 // Correction sweeps (iterative refinement against an FP64 base p0, FP32): the iterate is
 // e = p - p0, the gathers read e, and the update is
@@ -91,6 +95,13 @@ template <> struct WT<PolDF> {
   __device__ static float2 y(W w) { return df_from_double(w.y); }
 };
 
+// per warp: two block parities x (staged block of layer n-1, staged block of layer n+1),
+// each with 16 bytes of room for the copy's alignment offset
+template <class V>
+constexpr int kSlotBytes() {
+  return 4 * (HQ_MAX_BLOCK * (int)sizeof(typename V::T) + 16);
+}
+
 struct SweepArgs {
   int N, L, H, nsweeps, order, nphases;
   double lam;
@@ -102,6 +113,7 @@ struct SweepArgs {
   int pbfirst[HQ_MAXN + 2];    // rank blocks of phase ph: [pbfirst[ph], pbfirst[ph+1])
   const uint2* items;
   const int* blocks;           // first item of each rank block (and the end)
+  const int* perm;             // per phase, its blocks by decreasing cost
   const uint32_t* RL;
   const uint32_t* RH;
   const void* T;
@@ -138,10 +150,11 @@ struct Smem {
   int woff[HQ_LO_BITS + 2];         // woff[w + 1] - woff[w] = C(L, w)
   T nu[HQ_MAXN];
   int64_t off[HQ_MAXN + 2], toff[HQ_MAXN + 2], tw[HQ_MAXN + 2];
-  // per warp, for its current rank block: the high-part neighbour runs (busy units in
-  // increasing order, then idle units), and the idle units' rates at the same index
-  const T* hptr[kWarps][kHP];
-  T hnu[kWarps][kHP];
+  // per warp and block parity (a warp holds the rank block of its current item and of
+  // its next one): the high-part neighbour runs (busy units in increasing order, then idle
+  // units), and the idle units' rates at the same index
+  const T* hptr[kWarps][2][kHP];
+  T hnu[kWarps][2][kHP];
   double ws[kWarps][kMaxPL][4];     // per warp: layer sums of this phase
   float wmd[kWarps];
   double fold[kMaxWords];
@@ -232,42 +245,71 @@ __device__ __forceinline__ double2 ld_vec(const double2* p) { return __ldcs(p); 
 // neighbours by table slot (low units, then high units: slot W + j), idle neighbours by
 // unit (low, then high).  tv: the state's table record; h: its high-part neighbours (busy
 // units first, as the warp's list); lx: its low-part positions and idle units.
+// The low- and high-part sums run as separate chains (then low + high), which halves the
+// dependent FMA chain of a state; inside each part the order is by slot / by unit.
 template <int W, class V, int kHP, int kNV>
 __device__ __forceinline__ void inflows(typename V::T& U, typename V::T& D, const typename Vec<V>::VT* tv,
                                         const typename V::T* h, const uint4& lx, const typename V::T* sdn,
                                         const typename V::T* sup, int nbh, int H, int L,
                                         const typename V::T* nu, const typename V::T* hnu) {
+  typedef typename V::T T;
   constexpr int kMaxSlot = kNV * Vec<V>::kPer;
+  T Ul = V::zero(), Uh = V::zero(), Dl = V::zero(), Dh = V::zero();
 #pragma unroll
   for (int k = 0; k < W; k++) {
     const uint32_t pos = (lx_word(lx, k >> 2) >> (8 * (k & 3))) & 0xffu;
-    V::fma_acc(U, sdn[pos], Vec<V>::get(tv, k));
+    V::fma_acc(Ul, sdn[pos], Vec<V>::get(tv, k));
   }
 #pragma unroll
   for (int j = 0; j < kHP; j++) {
     if (j >= nbh) break;
-    if (W + j < kMaxSlot) V::fma_acc(U, h[j], Vec<V>::get(tv, W + j));
+    if (W + j < kMaxSlot) V::fma_acc(Uh, h[j], Vec<V>::get(tv, W + j));
   }
 #pragma unroll
   for (int k = W; k < HQ_LO_BITS; k++) {
     if (k >= L) break;
     const uint32_t pos = (lx_word(lx, k >> 2) >> (8 * (k & 3))) & 0xffu;
     const uint32_t u = (lx_word(lx, (80 + 4 * k) >> 5) >> ((80 + 4 * k) & 31)) & 0xfu;
-    V::fma_acc(D, sup[pos], nu[u]);
+    V::fma_acc(Dl, sup[pos], nu[u]);
   }
 #pragma unroll
   for (int j = 0; j < kHP; j++) {
     if (j >= H) break;
     if (j < nbh) continue;
-    V::fma_acc(D, h[j], hnu[j]);
+    V::fma_acc(Dh, h[j], hnu[j]);
   }
+  U = V::add(V::norm(Ul), V::norm(Uh));
+  D = V::add(V::norm(Dl), V::norm(Dh));
 }
 
+// One item's loads, held in registers from issue to compute.
+template <class V, int kNV, int kHP>
+struct ItemLoads {
+  typename Vec<V>::VT tv[kNV];  // the states' table records
+  typename V::T h[kHP];         // high-part neighbours (the block's list order)
+  typename V::T rv, po, q0, q1, q2;
+  typename WT<V>::W wv;
+};
+// A rank block as a warp holds it: its id bits, layer, base rank and high-part rates.
+template <class V>
+struct BlockCtx {
+  uint32_t hi, hself;
+  int w, n, nbh, par, grp;  // par: list/slot parity; grp: its cp.async group number
+  int od, ou;               // byte offsets of the staged blocks' first elements
+  typename V::T mu_hi;
+};
+struct ItemRef {
+  uint32_t rk;  // this lane's state rank in layer n
+  int cnt, bq;  // states in the item; which held block (0/1) it belongs to
+};
+
 // Process the rank blocks [b0, b1) of a phase whose layers start at f (li = (n - f) >>
-// order), dealt round-robin to the warps of the grid: block b0 + g, b0 + g + nwarps, ...
-// for warp g, so that at any time the warps work on neighbouring blocks (the table and
-// neighbour reads stay within a window of the layer) and each warp stages a block once
-// for all of its items.  One lane per state of an item.
+// order).  The phase's blocks come by decreasing cost (a.perm) and go to the warps in
+// snake order: round r gives block r W + g (r even) or r W + W - 1 - g (r odd) to warp g,
+// so the warps' totals even out.  A warp walks its blocks' items in order: per item it
+// issues every load (table record, high-part neighbours, r, the old value, the weights)
+// and then computes.  A block's neighbour lists and staged low-part blocks alternate
+// between two parities.  One lane per state of an item.
 // kMode 0: a sweep (write p, add the layer sums into s.ws);  kMode 1: a correction
 // sweep (the iterate is e, base terms from a.ir);  kMode 2: the base pass of the
 // refinement (read p = p0, write rho0, A0, B0 to a.out with the scalars c^0 in s.c1/c2;
@@ -282,22 +324,15 @@ __device__ __forceinline__ void run_items(Smem<V, kWarps, kHP>& s, const SweepAr
   typedef typename WX::W W;
   typedef typename Vec<V>::VT VT;
   constexpr int kNV = (kHP + HQ_LO_BITS + Vec<V>::kPer - 1) / Vec<V>::kPer;  // record vectors, at most
+  constexpr int kHalf = HQ_MAX_BLOCK * (int)sizeof(T) + 16;                // one staged block
   const int L = a.L, H = a.H, wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const T* pv = (const T*)a.p;
   T* pw = (T*)a.p;
   const bool relax = kMode != 2 && a.omega != 1.0;
   const T om = V::from_d(a.omega);
-  int cur_n = -1, li = 0, nvec = 0;
-  const T *p_dn = nullptr, *p_up = nullptr, *Tn = nullptr, *rn = nullptr;
-  T* p_n = nullptr;
-  const W* wn = nullptr;
-  const float* irn = nullptr;
-  float* outn = nullptr;
-  int64_t tw = 0;
-  T c1 = V::zero(), c2 = V::zero(), d1 = V::zero(), d2 = V::zero();
+  (void)kSlot;
+  int cur_n = -1, li = 0;
   T aS = V::zero(), aM = V::zero(), aW = V::zero(), aV = V::zero();
-  const T* sdn = (const T*)slot;
-  const T* sup = (const T*)(slot + kSlot / 2);
   auto flush = [&]() {
     if (kMode == 2) return;
     T v[4] = {aS, aM, aW, aV};
@@ -309,150 +344,186 @@ __device__ __forceinline__ void run_items(Smem<V, kWarps, kHP>& s, const SweepAr
     }
   };
   const int gwarp = (int)blockIdx.x * kWarps + wid, nwarps = (int)gridDim.x * kWarps;
-  for (int blk = b0 + gwarp; blk < b1; blk += nwarps) {
-    const int ib = __ldg(a.blocks + blk), ie = __ldg(a.blocks + blk + 1);
-    const uint2 d0 = __ldg(a.items + ib);
-    const uint32_t hi = d0.x & ((1u << HQ_SW_HI_BITS) - 1u);
-    const int w = (int)((d0.x >> HQ_SW_HI_BITS) & 0xfu);
-    const int n = (int)(d0.y >> 27);
-    if (n != cur_n) {
-      if (cur_n >= 0) flush();
-      cur_n = n;
-      li = (n - f) >> a.order;
-      p_dn = pv + s.off[n - 1];
-      p_up = pv + s.off[n + 1];
-      p_n = pw + s.off[n];
-      Tn = (const T*)a.T + s.toff[n];
-      tw = s.tw[n];
-      nvec = (int)tw / Vec<V>::kPer;
-      rn = (const T*)a.r + s.off[n];
-      wn = (const W*)a.wv + s.off[n];
-      c1 = s.c1[n];
-      c2 = s.c2[n];
-      if constexpr (kMode == 1) {
-        d1 = s.d1[n];
-        d2 = s.d2[n];
-        irn = a.ir + s.off[n];
-      }
-      if constexpr (kMode == 2) outn = a.out + s.off[n];
-      aS = aM = aW = aV = V::zero();
-    }
-    // the block: its neighbour block bases from RH (lane j < H: across high unit L + j;
-    // lanes 29..31: its own block and the blocks (hi, w -/+ 1)), the list of high-part
-    // runs, and the two low-part blocks staged in the warp's slot
-    __syncwarp();  // every lane is done with the previous block's staged values and lists
+  const int nb = b1 - b0;
+  // the warp's item sequence: its blocks in snake order, each block's items in order
+  int sr = 0, sit = 0, sie = 0;  // round, next item, end of the current block
+  auto block_of_round = [&](int r) -> int {
+    const int k = r * nwarps + ((r & 1) ? nwarps - 1 - gwarp : gwarp);
+    return k < nb ? __ldg(a.perm + b0 + k) : -1;
+  };
+  BlockCtx<V> bc0, bc1;  // the held blocks, by parity (selected by value: no local memory)
+  int ngrp = 0;        // cp.async groups committed so far
+  int last_par = 1;    // parity of the most recently set-up block
+  // set up block blk in the next parity: returns which held block (0/1) it is
+  auto setup = [&](int blk) -> int {
+    const int par = last_par ^ 1;
+    last_par = par;
+    const uint2 d0 = __ldg(a.items + __ldg(a.blocks + blk));
+    BlockCtx<V> c;
+    c.hi = d0.x & ((1u << HQ_SW_HI_BITS) - 1u);
+    c.w = (int)((d0.x >> HQ_SW_HI_BITS) & 0xfu);
+    c.n = (int)(d0.y >> 27);
+    c.par = par;
+    const uint32_t hi = c.hi;
+    const int w = c.w, n = c.n;
+    const T* p_dn = pv + s.off[n - 1];
+    const T* p_up = pv + s.off[n + 1];
+    __syncwarp();  // every lane is done with this parity's previous block
     int idx = -1;
     if (lane < H) idx = (int)((hi ^ (1u << lane)) * (uint32_t)(L + 1)) + w;
     else if (lane == 29) idx = (int)(hi * (uint32_t)(L + 1)) + w;
     else if (lane == 30 && w >= 1) idx = (int)(hi * (uint32_t)(L + 1)) + w - 1;
     else if (lane == 31 && w < L) idx = (int)(hi * (uint32_t)(L + 1)) + w + 1;
     const uint32_t rh = idx >= 0 ? __ldg(a.RH + idx) : 0u;
-    const int nbh = __popc(hi);
+    c.nbh = __popc(hi);
     T muj = V::zero();
     if (lane < H) {
       const int before = __popc(hi & ((1u << lane) - 1u));
       if ((hi >> lane) & 1u) {
-        s.hptr[wid][before] = p_dn + rh;
+        s.hptr[wid][par][before] = p_dn + rh;
         muj = s.nu[L + lane];
       } else {
-        const int at = nbh + lane - before;
-        s.hptr[wid][at] = p_up + rh;
-        s.hnu[wid][at] = s.nu[L + lane];
+        const int at = c.nbh + lane - before;
+        s.hptr[wid][par][at] = p_up + rh;
+        s.hnu[wid][par][at] = s.nu[L + lane];
       }
     }
     for (int m = 16; m > 0; m >>= 1) muj = V::add(muj, V::shfl_xor(muj, m));
-    const T mu_hi = muj;
-    const uint32_t hself = __shfl_sync(kFull, rh, 29);
-    {
-      const uint32_t bdn = __shfl_sync(kFull, rh, 30), bup = __shfl_sync(kFull, rh, 31);
-      const int dc = w >= 1 ? s.woff[w] - s.woff[w - 1] : 0;
-      const int uc = w < L ? s.woff[w + 2] - s.woff[w + 1] : 0;
-      const unsigned char* gd = (const unsigned char*)(p_dn + bdn);
-      const unsigned char* gu = (const unsigned char*)(p_up + bup);
-      const int od = (int)((uintptr_t)gd & 15u), ou = (int)((uintptr_t)gu & 15u);
-      const int cd = dc ? (od + dc * (int)sizeof(T) + 15) >> 4 : 0;
-      const int cu = uc ? (ou + uc * (int)sizeof(T) + 15) >> 4 : 0;
-      for (int c = lane; c < cd; c += 32) cp_async16(slot + 16 * c, gd - od + 16 * c);
-      for (int c = lane; c < cu; c += 32) cp_async16(slot + kSlot / 2 + 16 * c, gu - ou + 16 * c);
-      sdn = (const T*)(slot + od);
-      sup = (const T*)(slot + kSlot / 2 + ou);
-    }
-    bool staged = true;
+    c.mu_hi = muj;
+    c.hself = __shfl_sync(kFull, rh, 29);
+    const uint32_t bdn = __shfl_sync(kFull, rh, 30), bup = __shfl_sync(kFull, rh, 31);
+    const int dc = w >= 1 ? s.woff[w] - s.woff[w - 1] : 0;
+    const int uc = w < L ? s.woff[w + 2] - s.woff[w + 1] : 0;
+    const unsigned char* gd = (const unsigned char*)(p_dn + bdn);
+    const unsigned char* gu = (const unsigned char*)(p_up + bup);
+    const int od = (int)((uintptr_t)gd & 15u), ou = (int)((uintptr_t)gu & 15u);
+    const int cd = dc ? (od + dc * (int)sizeof(T) + 15) >> 4 : 0;
+    const int cu = uc ? (ou + uc * (int)sizeof(T) + 15) >> 4 : 0;
+    unsigned char* sl = slot + (size_t)par * 2 * kHalf;
+    for (int q = lane; q < cd; q += 32) cp_async16(sl + 16 * q, gd - od + 16 * q);
+    for (int q = lane; q < cu; q += 32) cp_async16(sl + kHalf + 16 * q, gu - ou + 16 * q);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    c.grp = ngrp++;
+    c.od = od;
+    c.ou = ou;
+    if (par) bc1 = c;
+    else bc0 = c;
     __syncwarp();  // the lists are visible to the warp
-    for (int it = ib; it < ie; it++) {
-      const uint2 d = it == ib ? d0 : __ldg(a.items + it);
-      const int cnt = (int)((d.x >> 22) & 0x3fu) + 1;
-      // this lane's state (lanes past the item repeat its first state and discard it)
-      const bool act = lane < cnt;
-      const uint32_t rk = (d.y & ((1u << 27) - 1u)) + (act ? (uint32_t)lane : 0u);
-      const uint32_t rib = rk - hself;
-      // every load of the item before the wait: the table record (vectors), the high-part
-      // neighbours, r, the old value, the weights
-      const VT* rec = (const VT*)(Tn + (int64_t)rk * tw);
-      VT tv[kNV];
+    return par;
+  };
+  // advance the sequence; false at its end
+  auto next_item = [&](int& it_out, bool& newblk) -> bool {
+    newblk = false;
+    if (sit >= sie) {
+      const int blk = block_of_round(sr);
+      if (blk < 0) return false;
+      sr++;
+      sit = __ldg(a.blocks + blk);
+      sie = __ldg(a.blocks + blk + 1);
+      setup(blk);
+      newblk = true;
+    }
+    it_out = sit++;
+    return true;
+  };
+  // issue every load of item `it` of the block in parity bq
+  auto issue = [&](int it, int bq, ItemRef& ir, ItemLoads<V, kNV, kHP>& ld) {
+    const BlockCtx<V> c = bq ? bc1 : bc0;
+    const uint2 d = __ldg(a.items + it);
+    ir.cnt = (int)((d.x >> 22) & 0x3fu) + 1;
+    ir.bq = bq;
+    const bool act = lane < ir.cnt;
+    ir.rk = (d.y & ((1u << 27) - 1u)) + (act ? (uint32_t)lane : 0u);
+    const uint32_t rib = ir.rk - c.hself;
+    const int n = c.n;
+    const int64_t tw = s.tw[n];
+    const int nvec = (int)tw / Vec<V>::kPer;
+    const VT* rec = (const VT*)((const T*)a.T + s.toff[n] + (int64_t)ir.rk * tw);
 #pragma unroll
-      for (int v = 0; v < kNV; v++) {
-        if (v >= nvec) break;
-        tv[v] = ld_vec(rec + v);
-      }
-      T h[kHP];
+    for (int v = 0; v < kNV; v++) {
+      if (v >= nvec) break;
+      ld.tv[v] = ld_vec(rec + v);
+    }
 #pragma unroll
-      for (int j = 0; j < kHP; j++) {
-        if (j >= H) break;
-        h[j] = ld_l2(s.hptr[wid][j] + rib);
-      }
-      const T rv = ld_stream(rn + rk);
-      const T po = ld_l2(p_n + rk);
-      W wv = {};
-      if constexpr (kMode != 2) wv = __ldcs(wn + rk);
-      T q0 = V::zero(), q1 = V::zero(), q2 = V::zero();
-      if constexpr (kMode == 1) {
-        q0 = ld_stream(irn + rk);
-        q1 = ld_stream(irn + a.Sp + rk);
-        q2 = ld_stream(irn + 2 * a.Sp + rk);
-      }
-      if (staged) {
-        cp_async_wait_all();
-        __syncwarp();
-        staged = false;
-      }
-      const int ent = s.woff[w] + (int)rib;
-      const uint4 lx = s.LX[ent];
-      T U = V::zero(), D = V::zero();
-      switch (w) {
+    for (int j = 0; j < kHP; j++) {
+      if (j >= H) break;
+      ld.h[j] = ld_l2(s.hptr[wid][bq][j] + rib);
+    }
+    const int64_t on = s.off[n];
+    ld.rv = ld_stream((const T*)a.r + on + ir.rk);
+    ld.po = ld_l2(pv + on + ir.rk);
+    if constexpr (kMode != 2) ld.wv = __ldcs((const W*)a.wv + on + ir.rk);
+    if constexpr (kMode == 1) {
+      const float* irn = a.ir + on + ir.rk;
+      ld.q0 = ld_stream(irn);
+      ld.q1 = ld_stream(irn + a.Sp);
+      ld.q2 = ld_stream(irn + 2 * a.Sp);
+    }
+  };
+  // compute item ir from its loads
+  auto compute = [&](const ItemRef& ir, const ItemLoads<V, kNV, kHP>& ld) {
+    const BlockCtx<V> c = ir.bq ? bc1 : bc0;
+    // the block's staged low-part blocks: every group up to its own must be complete
+    if (ngrp - 1 - c.grp >= 1) asm volatile("cp.async.wait_group 1;" ::: "memory");
+    else asm volatile("cp.async.wait_group 0;" ::: "memory");
+    __syncwarp();
+    const int n = c.n, w = c.w;
+    if (n != cur_n) {
+      if (cur_n >= 0) flush();
+      cur_n = n;
+      li = (n - f) >> a.order;
+      aS = aM = aW = aV = V::zero();
+    }
+    const bool act = lane < ir.cnt;
+    const uint32_t rib = ir.rk - c.hself;
+    const int ent = s.woff[w] + (int)rib;
+    const uint4 lx = s.LX[ent];
+    const unsigned char* sl = slot + (size_t)ir.bq * 2 * kHalf;
+    const T* sdn = (const T*)(sl + c.od);
+    const T* sup = (const T*)(sl + kHalf + c.ou);
+    T U = V::zero(), D = V::zero();
+    switch (w) {
 #define HQ_INFLOWS(Wc) \
-  case Wc: inflows<Wc, V, kHP, kNV>(U, D, tv, h, lx, sdn, sup, nbh, H, L, s.nu, s.hnu[wid]); break;
-        HQ_INFLOWS(0) HQ_INFLOWS(1) HQ_INFLOWS(2) HQ_INFLOWS(3) HQ_INFLOWS(4) HQ_INFLOWS(5)
-        HQ_INFLOWS(6) HQ_INFLOWS(7) HQ_INFLOWS(8) HQ_INFLOWS(9) HQ_INFLOWS(10)
+  case Wc: inflows<Wc, V, kHP, kNV>(U, D, ld.tv, ld.h, lx, sdn, sup, c.nbh, H, L, s.nu, s.hnu[wid][ir.bq]); break;
+      HQ_INFLOWS(0) HQ_INFLOWS(1) HQ_INFLOWS(2) HQ_INFLOWS(3) HQ_INFLOWS(4) HQ_INFLOWS(5)
+      HQ_INFLOWS(6) HQ_INFLOWS(7) HQ_INFLOWS(8) HQ_INFLOWS(9) HQ_INFLOWS(10)
 #undef HQ_INFLOWS
-        default: break;
+      default: break;
+    }
+    const T A = V::mul(U, ld.rv), B = V::mul(D, ld.rv);
+    const T c1 = s.c1[n], c2 = s.c2[n];
+    if constexpr (kMode == 2) {
+      // base pass: rho0 = c1^0 A0 + c2^0 B0 - p0 (FP64 here), stored in FP32
+      if (act) {
+        float* outn = a.out + s.off[n] + ir.rk;
+        const double A0 = V::to_d(A), B0 = V::to_d(B);
+        const double rho0 = V::to_d(c1) * A0 + V::to_d(c2) * B0 - V::to_d(ld.po);
+        outn[0] = (float)rho0;
+        outn[a.Sp] = (float)A0;
+        outn[2 * a.Sp] = (float)B0;
       }
-      U = V::norm(U);
-      D = V::norm(D);
-      const T A = V::mul(U, rv), B = V::mul(D, rv);
-      if constexpr (kMode == 2) {
-        // base pass: rho0 = c1^0 A0 + c2^0 B0 - p0 (FP64 here), stored in FP32
-        if (act) {
-          const double A0 = V::to_d(A), B0 = V::to_d(B);
-          const double rho0 = V::to_d(c1) * A0 + V::to_d(c2) * B0 - V::to_d(po);
-          outn[rk] = (float)rho0;
-          outn[a.Sp + rk] = (float)A0;
-          outn[2 * a.Sp + rk] = (float)B0;
-        }
-      } else {
-        T pn = V::add(V::mul(c1, A), V::mul(c2, B));
-        if constexpr (kMode == 1) pn = V::add(V::add(q0, V::add(V::mul(d1, q1), V::mul(d2, q2))), pn);
-        if (relax) pn = V::add(po, V::mul(om, V::sub(pn, po)));
-        md = fmaxf(md, V::absdiff(pn, po));
-        if (act) {
-          p_n[rk] = pn;
-          aS = V::add(aS, pn);
-          aM = V::add(aM, V::mul(pn, V::add(s.MUlo[s.LO[ent]], mu_hi)));
-          aW = V::add(aW, V::mul(pn, WX::x(wv)));
-          aV = V::add(aV, V::mul(pn, WX::y(wv)));
-        }
+    } else {
+      T pn = V::add(V::mul(c1, A), V::mul(c2, B));
+      if constexpr (kMode == 1)
+        pn = V::add(V::add(ld.q0, V::add(V::mul(s.d1[n], ld.q1), V::mul(s.d2[n], ld.q2))), pn);
+      if (relax) pn = V::add(ld.po, V::mul(om, V::sub(pn, ld.po)));
+      md = fmaxf(md, V::absdiff(pn, ld.po));
+      if (act) {
+        pw[s.off[n] + ir.rk] = pn;
+        aS = V::add(aS, pn);
+        aM = V::add(aM, V::mul(pn, V::add(s.MUlo[s.LO[ent]], c.mu_hi)));
+        aW = V::add(aW, V::mul(pn, WX::x(ld.wv)));
+        aV = V::add(aV, V::mul(pn, WX::y(ld.wv)));
       }
     }
+  };
+  ItemLoads<V, kNV, kHP> LA;
+  ItemRef RA;
+  int it;
+  bool nbk;
+  while (next_item(it, nbk)) {
+    issue(it, last_par, RA, LA);
+    compute(RA, LA);
   }
   if (cur_n >= 0) flush();
 }
@@ -485,7 +556,7 @@ __device__ void solve_layer(Smem<V, kWarps, kHP>& s, const SweepArgs& a, int n) 
 template <class V, bool kIR, int kHP, int kThreads>
 __global__ void __launch_bounds__(kThreads, 1) k_sweep(SweepArgs a) {
   constexpr int kWarps = kThreads / 32;
-  constexpr int kSlot = 2 * (HQ_MAX_BLOCK * (int)sizeof(typename V::T) + 16);
+  constexpr int kSlot = kSlotBytes<V>();
   extern __shared__ __align__(128) unsigned char smem_dyn[];
   __shared__ Smem<V, kWarps, kHP> s;
   DevScalars* sc = a.sc;
@@ -618,7 +689,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_sweep(SweepArgs a) {
 template <int kHP, int kThreads>
 __global__ void __launch_bounds__(kThreads, 1) k_base_pass(SweepArgs a) {
   constexpr int kWarps = kThreads / 32;
-  constexpr int kSlot = 2 * (HQ_MAX_BLOCK * (int)sizeof(double) + 16);
+  constexpr int kSlot = kSlotBytes<PolF64>();
   extern __shared__ __align__(128) unsigned char smem_dyn[];
   __shared__ Smem<PolF64, kWarps, kHP> s;
   const int N = a.N;
@@ -789,29 +860,13 @@ __global__ void __launch_bounds__(256) k_weights(WeightArgs a, int64_t Sp) {
 
 constexpr int kSweepThreads = 512;
 
-// launch-shape experiment (FP32 sweeps, N <= 24): threads per CTA from HQ_SWEEP_THREADS
-int sweep_threads(int H, int kind) {
-  static int t = -1;
-  if (t < 0) {
-    const char* e = getenv("HQ_SWEEP_THREADS");
-    t = e ? atoi(e) : kSweepThreads;
-    if (t != 384 && t != 512 && t != 768 && t != 1024) t = kSweepThreads;
-  }
-  return (H <= 14 && kind == HQ_PREC_FP32) ? t : kSweepThreads;
-}
+// One CTA of 512 threads per SM (16 warps, up to 128 registers) for every precision:
+// measured on the FP32 sweep at N=24, 384 threads (with two items in flight per warp or
+// one) and 768 threads (spilling) were slower.
+int sweep_threads(int, int) { return kSweepThreads; }
 
 template <class V, bool kIR>
 const void* sweep_fn(int H) {
-  if constexpr (V::kind == HQ_PREC_FP32) {
-    if (H <= 14) {
-      switch (sweep_threads(H, V::kind)) {
-        case 384: return (const void*)k_sweep<V, kIR, 14, 384>;
-        case 768: return (const void*)k_sweep<V, kIR, 14, 768>;
-        case 1024: return (const void*)k_sweep<V, kIR, 14, 1024>;
-        default: break;
-      }
-    }
-  }
   if (H <= 14) return (const void*)k_sweep<V, kIR, 14, kSweepThreads>;
   return (const void*)k_sweep<V, kIR, 18, kSweepThreads>;
 }
@@ -836,6 +891,7 @@ void fill_args(hq_solver* h, SweepArgs& a, int order) {
   }
   a.items = h->sitems[order];
   a.blocks = h->sblocks[order];
+  a.perm = h->sperm[order];
   a.RL = h->RL;
   a.RH = h->RH;
   a.partials = h->partials;
@@ -849,7 +905,7 @@ template <class V>
 int launch_sweep(hq_solver* h, int nsweeps, cudaEvent_t ev0, cudaEvent_t ev1, int G, bool ir) {
   typedef typename V::T T;
   const int thr = sweep_threads(h->H, V::kind);
-  const size_t smem = (size_t)(thr / 32) * 2 * (HQ_MAX_BLOCK * sizeof(T) + 16);
+  const size_t smem = (size_t)(thr / 32) * kSlotBytes<V>();
   const void* kfn = ir ? sweep_fn<PolF32, true>(h->H) : sweep_fn<V, false>(h->H);
   PrecBufs& bp = hq_bufs(h, V::kind);
   SweepArgs a;
@@ -876,7 +932,7 @@ template <class V>
 int sweep_grid(hq_solver* h, bool ir, int* G) {
   typedef typename V::T T;
   const int thr = sweep_threads(h->H, V::kind);
-  const size_t smem = (size_t)(thr / 32) * 2 * (HQ_MAX_BLOCK * sizeof(T) + 16);
+  const size_t smem = (size_t)(thr / 32) * kSlotBytes<V>();
   const void* kfn = ir ? sweep_fn<PolF32, true>(h->H) : sweep_fn<V, false>(h->H);
   if (!g_nsm) HQ_CUDA(cudaDeviceGetAttribute(&g_nsm, cudaDevAttrMultiProcessorCount, h->dev));
   HQ_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -938,7 +994,7 @@ int hq_base_pass(hq_solver* h) {
   a.nu = h->b64.nu;
   a.wv = h->wv64;
   a.out = h->ir;
-  const size_t smem = (size_t)(kSweepThreads / 32) * 2 * (HQ_MAX_BLOCK * sizeof(double) + 16);
+  const size_t smem = (size_t)(kSweepThreads / 32) * kSlotBytes<PolF64>();
   const void* kfn = h->H <= 14 ? (const void*)k_base_pass<14, kSweepThreads>
                                : (const void*)k_base_pass<18, kSweepThreads>;
   HQ_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
