@@ -89,7 +89,8 @@ typedef struct hq_opts {
   int warm_mem;        /* hq_mem of warm_p */
   const double* warm_p;/* HQ_WARM_GIVEN: start vector p_n(B) in y-order, length 2^N */
   double fp32_stall;   /* mixed modes: leave FP32 when the step's decay per check is
-                          worse than this ratio (0 = default: 0.75 for HQ_PREC_FP32_IR,
+                          worse than this ratio at two checks in a row, or at one once
+                          the step is below 1e-6 (0 = default: 0.75 for HQ_PREC_FP32_IR,
                           whose correction sweeps cost about an FP32 sweep, 0.9 for
                           DF64 / FP64 refinement); HQ_PREC_FP32_IR
                           also re-bases when four checks in a row decay worse than it,
@@ -296,8 +297,8 @@ void hq_batch_destroy(hq_batch* b);
  * lambda s1_i / nu_i, lambda / sum nu, log(nu_i / mean nu), N / 16, and n / N.  hq_solve
  * with warm_start = HQ_WARM_MLP then starts from the layer-wise product form
  * p_n(B) = prod_{i in B} x_i(n) / e_n(x(n)), x_i(n) = q_i(n) / (1 - q_i(n)), and keeps it
- * only if its first sweep's step is no larger than that of a first sweep from the uniform
- * start (both probe sweeps are counted in the stats; stats.warm_used says which won).
+ * only if its FP64 relative balance residual of Eq. (1) is below the uniform start's
+ * (two residual evaluations, no sweep; stats.warm_used says which was kept).
  * warm_start = HQ_WARM_PRODUCT is the analytic control, with no network: the same
  * product form and fallback with q_i(n) = rho0_i for every layer, rho0_i the unit's
  * first-choice utilisation lambda1_i / nu_i clipped to [0.02, 0.98], lambda1_i the

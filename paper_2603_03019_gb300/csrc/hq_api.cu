@@ -327,7 +327,7 @@ extern "C" int hq_solve(hq_solver* h, const hq_opts* opts_in, hq_stats* stats) {
     case HQ_PREC_FP32_IR: phases[0] = HQ_PREC_FP32; phases[1] = HQ_PREC_IRC; nph = 2; break;
     default: phases[0] = HQ_PREC_FP32; phases[1] = HQ_PREC_FP64; nph = 2; break;
   }
-  int rebases = 0, ir_bases = 0, ir_flat = 0;
+  int rebases = 0, ir_bases = 0, ir_flat = 0, fp32_flat = 0;
   double step_base = 0.0;  // the first step of the current refinement base
   double last_ratio = 0.0;  // the step decay of the check before
   int phase_checks = 0;     // checks since the last change of precision or base
@@ -337,24 +337,19 @@ extern "C" int hq_solve(hq_solver* h, const hq_opts* opts_in, hq_stats* stats) {
   bool warm_kept = o.warm_start == HQ_WARM_GIVEN;
   int rc;
   if ((o.warm_start == HQ_WARM_MLP || o.warm_start == HQ_WARM_PRODUCT) && h->N >= 2) {
-    // the learned (or analytic) start is kept only if its first sweep moves the iterate
-    // no more than a first sweep from the paper's uniform start does; both probe sweeps
-    // are counted
+    // the learned (or analytic) start is kept only if it is closer to the fixed point than
+    // the paper's uniform start, by the FP64 relative balance residual of Eq. (1) of each
+    // (the judge of the plain iteration's error); no sweep is spent on the test
+    double res_cold = INFINITY, res_warm = INFINITY;
     rc = hq_init_iterate(h, phases[0], nullptr, HQ_HOST);
-    if (rc == HQ_OK) rc = hq_run_sweeps(h, phases[0], 1, nullptr, nullptr);
-    if (rc == HQ_OK) rc = pull_scalars(h);
+    if (rc == HQ_OK) rc = hq_compute_residual(h, &res_cold);
     if (rc != HQ_OK) return rc;
-    const double step_cold = h->hsc->step;
     rc = o.warm_start == HQ_WARM_MLP ? hq_mlp_warm_start(h, h->mlp, h->pcond, nullptr)
                                      : hq_product_warm_start(h, h->pcond);
     if (rc == HQ_OK) rc = hq_init_iterate(h, phases[0], h->pcond, HQ_DEVICE);
-    if (rc == HQ_OK) rc = hq_run_sweeps(h, phases[0], 1, nullptr, nullptr);
-    if (rc == HQ_OK) rc = pull_scalars(h);
+    if (rc == HQ_OK) rc = hq_compute_residual(h, &res_warm);
     if (rc != HQ_OK) return rc;
-    const double step_warm = h->hsc->step;
-    sweeps[phases[0] == HQ_PREC_FP32 ? 0 : 1] += 2;
-    total = 2;
-    warm_kept = isfinite(step_warm) && step_warm <= step_cold;
+    warm_kept = isfinite(res_warm) && res_warm < res_cold;
     if (!warm_kept) {
       rc = hq_init_iterate(h, phases[0], nullptr, HQ_HOST);
       if (rc != HQ_OK) return rc;
@@ -402,12 +397,14 @@ extern "C" int hq_solve(hq_solver* h, const hq_opts* opts_in, hq_stats* stats) {
     // leave FP32 once its steps stop shrinking geometrically (rounding floor); correction
     // sweeps cost about what FP32 sweeps cost, so refinement by them also starts when
     // the decay turns abruptly worse than the check before (past the start's transient)
-    const bool leave =
-        !last_phase &&
-        (step == 0.0 ||
-         (prev_check_step > 0.0 &&
-          (ratio > stall || (phases[ph + 1] == HQ_PREC_IRC && checks > 4 && last_ratio > 0.0 &&
-                             ratio > 0.5 && ratio > 1.5 * last_ratio))));
+    // A slowly decaying error (a warm start's, or any slow mode) also gives a poor decay
+    // ratio: one poor check ends FP32 only once the step is near FP32 resolution (1e-6 of
+    // a probability), otherwise two in a row must
+    const bool poor = prev_check_step > 0.0 &&
+                      (ratio > stall || (phases[ph + 1] == HQ_PREC_IRC && checks > 4 && last_ratio > 0.0 &&
+                                         ratio > 0.5 && ratio > 1.5 * last_ratio));
+    fp32_flat = poor ? fp32_flat + 1 : 0;
+    const bool leave = !last_phase && (step == 0.0 || (poor && (step < 1e-6 || fp32_flat >= 2)));
     if (auto_omega) {
       // Young's optimal relaxation for the observed contraction: with Algorithm 1's
       // per-sweep rate r (measured over the third check, past the start's transient),
@@ -431,6 +428,7 @@ extern "C" int hq_solve(hq_solver* h, const hq_opts* opts_in, hq_stats* stats) {
         if (rc != HQ_OK) return rc;
         if (phases[ph + 1] == HQ_PREC_IRC) ir_bases++;
         ph++;
+        fp32_flat = 0;
         prev_check_step = 0.0;
         last_ratio = 0.0;
         phase_checks = 0;

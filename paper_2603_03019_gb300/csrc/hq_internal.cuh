@@ -325,6 +325,7 @@ int hq_product_warm_start(hq_solver* h, double* P);  // the analytic control (HQ
 int hq_ir_begin(hq_solver* h, int from);
 int hq_ir_assemble(hq_solver* h);
 int hq_base_pass(hq_solver* h);  // base scalars c^0 and the FP32 base terms (hq_persist.cu)
+int hq_residual_fused(hq_solver* h);  // residual maxima of layers 1..N-1 into res_num/res_den[1]
 
 // work items and low-part positions of the sweep (hq_items.cu)
 int hq_item_list(int N, std::vector<uint4>& items, int* ifirst);  // host list, layer by layer

@@ -163,6 +163,7 @@ struct Smem {
   double I1[HQ_MAXN + 1], I2[HQ_MAXN + 1];  // corrections: c1^0, c2^0
   T c1[HQ_MAXN + 1], c2[HQ_MAXN + 1], d1[HQ_MAXN + 1], d2[HQ_MAXN + 1];
   double step[2];
+  double fac[HQ_MAXN + 1];          // residual: P{B} = fac[w(B)] p(B)
 };
 
 template <class V, int kWarps, int kHP>
@@ -313,12 +314,14 @@ struct ItemRef {
 // kMode 0: a sweep (write p, add the layer sums into s.ws);  kMode 1: a correction
 // sweep (the iterate is e, base terms from a.ir);  kMode 2: the base pass of the
 // refinement (read p = p0, write rho0, A0, B0 to a.out with the scalars c^0 in s.c1/c2;
-// no sums, no update).  md receives the step max |p_new - p_old|.
+// no sums, no update);  kMode 3: the global-balance residual of Eq. (1) (read p, FP64;
+// md and rmax receive max_m |out_m - in_m| and max_m out_m).  md receives the step max
+// |p_new - p_old| in modes 0 and 1.
 // Every per-neighbour loop is unrolled with compile-time indices (registers) and leaves
 // at a warp-uniform bound, so only the neighbours that exist issue instructions.
 template <class V, int kMode, int kHP, int kWarps>
 __device__ __forceinline__ void run_items(Smem<V, kWarps, kHP>& s, const SweepArgs& a, int b0, int b1, int f,
-                                          unsigned char* slot, int kSlot, float& md) {
+                                          unsigned char* slot, int kSlot, float& md, double* rmax = nullptr) {
   typedef typename V::T T;
   typedef WT<V> WX;
   typedef typename WX::W W;
@@ -452,7 +455,7 @@ __device__ __forceinline__ void run_items(Smem<V, kWarps, kHP>& s, const SweepAr
     const int64_t on = s.off[n];
     ld.rv = ld_stream((const T*)a.r + on + ir.rk);
     ld.po = ld_l2(pv + on + ir.rk);
-    if constexpr (kMode != 2) ld.wv = __ldcs((const W*)a.wv + on + ir.rk);
+    if constexpr (kMode < 2) ld.wv = __ldcs((const W*)a.wv + on + ir.rk);
     if constexpr (kMode == 1) {
       const float* irn = a.ir + on + ir.rk;
       ld.q0 = ld_stream(irn);
@@ -492,7 +495,17 @@ __device__ __forceinline__ void run_items(Smem<V, kWarps, kHP>& s, const SweepAr
     }
     const T A = V::mul(U, ld.rv), B = V::mul(D, ld.rv);
     const T c1 = s.c1[n], c2 = s.c2[n];
-    if constexpr (kMode == 2) {
+    if constexpr (kMode == 3) {
+      // Eq. (1) at this state: out = P (lambda + mu_m), in = P-weighted inflows from its
+      // neighbours, P = fac[layer] p (lambda_m = lambda in layers 1..N-1)
+      const double mu = V::to_d(s.MUlo[s.LO[ent]]) + V::to_d(c.mu_hi);
+      const double out = s.fac[n] * V::to_d(ld.po) * (a.lam + mu);
+      const double in = s.fac[n - 1] * V::to_d(U) + s.fac[n + 1] * V::to_d(D);
+      if (act) {
+        rmax[0] = fmax(rmax[0], fabs(out - in));
+        rmax[1] = fmax(rmax[1], out);
+      }
+    } else if constexpr (kMode == 2) {
       // base pass: rho0 = c1^0 A0 + c2^0 B0 - p0 (FP64 here), stored in FP32
       if (act) {
         float* outn = a.out + s.off[n] + ir.rk;
@@ -703,6 +716,35 @@ __global__ void __launch_bounds__(kThreads, 1) k_base_pass(SweepArgs a) {
   __syncthreads();
   float md = 0.f;
   run_items<PolF64, 2, kHP, kWarps>(s, a, a.pbfirst[0], a.pbfirst[a.nphases], 1, slot, kSlot, md);
+}
+
+// The relative global-balance residual's maxima over layers 1..N-1 (Eq. 1): the same
+// gather as a sweep, from the FP64 iterate, with P = fac[n] p; per warp a max, folded by
+// atomic maxima on the bit patterns of the non-negative doubles into res_num[1],
+// res_den[1] (zeroed by the caller)
+template <int kHP, int kThreads>
+__global__ void __launch_bounds__(kThreads, 1) k_residual_fused(SweepArgs a) {
+  constexpr int kWarps = kThreads / 32;
+  constexpr int kSlot = kSlotBytes<PolF64>();
+  extern __shared__ __align__(128) unsigned char smem_dyn[];
+  __shared__ Smem<PolF64, kWarps, kHP> s;
+  const int N = a.N;
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  unsigned char* slot = smem_dyn + (size_t)wid * kSlot;
+  setup_tables(s, a);
+  for (int n = threadIdx.x; n <= N; n += kThreads) s.fac[n] = a.sc->fac[n];
+  __syncthreads();
+  float md = 0.f;
+  double rm[2] = {0.0, 0.0};
+  run_items<PolF64, 3, kHP, kWarps>(s, a, a.pbfirst[0], a.pbfirst[a.nphases], 1, slot, kSlot, md, rm);
+  for (int m = 16; m > 0; m >>= 1) {
+    rm[0] = fmax(rm[0], __shfl_xor_sync(kFull, rm[0], m));
+    rm[1] = fmax(rm[1], __shfl_xor_sync(kFull, rm[1], m));
+  }
+  if (lane == 0) {
+    atomicMax((unsigned long long*)&a.sc->res_num[1], (unsigned long long)__double_as_longlong(rm[0]));
+    atomicMax((unsigned long long*)&a.sc->res_den[1], (unsigned long long)__double_as_longlong(rm[1]));
+  }
 }
 
 // base scalars c^0 of every layer from the base's layer sums (Jacobi: all from p0)
@@ -999,6 +1041,28 @@ int hq_base_pass(hq_solver* h) {
                                : (const void*)k_base_pass<18, kSweepThreads>;
   HQ_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   if (!g_nsm) HQ_CUDA(cudaDeviceGetAttribute(&g_nsm, cudaDevAttrMultiProcessorCount, h->dev));
+  void* args[] = {&a};
+  HQ_CUDA(cudaLaunchKernel(kfn, dim3(g_nsm), dim3(kSweepThreads), args, smem, h->stream));
+  HQ_LAUNCHED();
+  return HQ_OK;
+}
+
+int hq_residual_fused(hq_solver* h) {
+  if (h->N < 2) return HQ_OK;
+  if (!g_nsm) HQ_CUDA(cudaDeviceGetAttribute(&g_nsm, cudaDevAttrMultiProcessorCount, h->dev));
+  SweepArgs a;
+  fill_args(h, a, HQ_ORDER_ASCENDING);
+  a.T = h->b64.T;
+  a.r = h->b64.r;
+  a.p = h->b64.p;
+  a.nu = h->b64.nu;
+  a.wv = h->wv64;
+  HQ_CUDA(cudaMemsetAsync(&h->sc->res_num[0], 0, sizeof(double) * (HQ_MAXN + 1), h->stream));
+  HQ_CUDA(cudaMemsetAsync(&h->sc->res_den[0], 0, sizeof(double) * (HQ_MAXN + 1), h->stream));
+  const size_t smem = (size_t)(kSweepThreads / 32) * kSlotBytes<PolF64>();
+  const void* kfn = h->H <= 14 ? (const void*)k_residual_fused<14, kSweepThreads>
+                               : (const void*)k_residual_fused<18, kSweepThreads>;
+  HQ_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   void* args[] = {&a};
   HQ_CUDA(cudaLaunchKernel(kfn, dim3(g_nsm), dim3(kSweepThreads), args, smem, h->stream));
   HQ_LAUNCHED();

@@ -462,7 +462,12 @@ static int residual_pass(hq_solver* h) {
     HQ_CUDA(cudaStreamSynchronize(h->stream));
     pq1_nusum = v * h->nu_sum;
   }
+  // layers 1..N-1 in one pass with the sweep's gather (fused kernel, hq_persist.cu); it
+  // zeroes every layer's maxima first.  Layers 0 and N (one state each) by k_residual.
+  int rc = hq_residual_fused(h);
+  if (rc != HQ_OK) return rc;
   for (int n = 0; n <= h->N; n++) {
+    if (h->N >= 2 && n > 0 && n < h->N) continue;
     ResArgs a;
     a.N = h->N;
     a.L = h->L;

@@ -329,8 +329,9 @@ def test_relaxation_saves_sweeps_and_rejects_bad_omega(gpu_lib):
 def test_refinement_matches_fp64_and_rebases(gpu_lib):
     """FP32 correction sweeps reach the FP64 fixed point: the refined N=20 solution agrees
     with plain FP64 sweeps and the oracle; a stall threshold that declares every check
-    stalled switches to refinement after 16 FP32 sweeps, far from the solution, so the
-    first correction meets its FP32 floor early and the base must absorb it again."""
+    stalled switches to refinement after 24 FP32 sweeps (the first check has no decay to
+    judge, the next two stall in a row), far from the solution, so the first correction
+    meets its FP32 floor early and the base must absorb it again."""
     inst = I.mixed_n20(2001, 0.6)
     s = hq.Solver.for_instance(inst)
     rc, ref = s.solve(tol=1e-13, precision="fp64", omega=-1.0)
@@ -346,7 +347,7 @@ def test_refinement_matches_fp64_and_rebases(gpu_lib):
     assert np.max(np.abs(s.utilisation() - rho64)) < 1e-10
     rc, st2 = s.solve(tol=1e-13, precision="fp32+ir", fp32_stall=1e-3, max_sweeps=800)
     assert rc == hq.HQ_OK, st2
-    assert st2["sweeps_fp32"] == 16 and 2 <= st2["ir_bases"] <= 4
+    assert st2["sweeps_fp32"] == 24 and 2 <= st2["ir_bases"] <= 4
     assert np.max(np.abs(s.stationary() - P64)) < 1e-11
     r = oracle.solve(inst, eps=1e-15, threads=0)
     assert np.max(np.abs(P64 - r["P"])) < 1e-10
