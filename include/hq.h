@@ -128,6 +128,10 @@ typedef struct hq_stats {
   int warm_used;          /* 1 if a warm start was kept, 0 if cold (or fell back) */
   int ir_bases;           /* HQ_PREC_FP32_IR: FP64 bases the refinement set up (0 otherwise) */
   double omega;           /* over-relaxation in use at the end of the solve */
+  double ms_sweeps_fp32;  /* device time of the FP32 sweep launches (CUDA events on the
+                             solver's stream around each launch; hq_solve only, 0 in
+                             hq_batch_solve) */
+  double ms_sweeps_hi;    /* the same for the refinement phase's sweep launches */
   int reserved[2];
 } hq_stats;
 

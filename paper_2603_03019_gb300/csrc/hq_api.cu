@@ -69,6 +69,8 @@ static void free_all(hq_solver* h) {
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->hsc) cudaFreeHost(h->hsc);
+  for (cudaEvent_t& e : h->kev)
+    if (e) cudaEventDestroy(e), e = nullptr;
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
 }
 
@@ -333,6 +335,9 @@ extern "C" int hq_solve(hq_solver* h, const hq_opts* opts_in, hq_stats* stats) {
   int phase_checks = 0;     // checks since the last change of precision or base
   int ph = 0;
   int sweeps[2] = {0, 0};
+  double kernel_ms[2] = {0.0, 0.0};
+  for (cudaEvent_t& e : h->kev)
+    if (!e) HQ_CUDA(cudaEventCreate(&e));
   int total = 0, checks = 0, res_checks = 0, since_res = 0, stalled = 0;
   bool warm_kept = o.warm_start == HQ_WARM_GIVEN;
   int rc;
@@ -372,11 +377,18 @@ extern "C" int hq_solve(hq_solver* h, const hq_opts* opts_in, hq_stats* stats) {
     const int prec = phases[ph];
     int nrun = o.check_every;
     if (nrun > o.max_sweeps - total) nrun = o.max_sweeps - total;
-    rc = hq_run_sweeps(h, prec, nrun, nullptr, nullptr);
+    rc = hq_run_sweeps(h, prec, nrun, h->kev[0], h->kev[1]);
     h->dbg_skip_cta = -1;
     if (rc != HQ_OK) return rc;
     rc = pull_scalars(h);
     if (rc != HQ_OK) return rc;
+    {
+      // device time of this launch (the scalars' read-back synchronised the stream)
+      float kms = 0.0f;
+      if (h->N >= 2 && cudaEventElapsedTime(&kms, h->kev[0], h->kev[1]) == cudaSuccess)
+        kernel_ms[prec == HQ_PREC_FP32 ? 0 : 1] += kms;
+      cudaGetLastError();
+    }
     total += nrun;
     sweeps[prec == HQ_PREC_FP32 ? 0 : 1] += nrun;
     checks++;
@@ -523,6 +535,8 @@ extern "C" int hq_solve(hq_solver* h, const hq_opts* opts_in, hq_stats* stats) {
     stats->warm_used = warm_kept ? 1 : 0;
     stats->ir_bases = ir_bases;
     stats->omega = h->omega;
+    stats->ms_sweeps_fp32 = kernel_ms[0];
+    stats->ms_sweeps_hi = kernel_ms[1];
   }
   (void)checks;
   return status;

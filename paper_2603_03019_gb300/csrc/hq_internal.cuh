@@ -265,6 +265,7 @@ struct hq_solver {
   int order = HQ_ORDER_ASCENDING;  // sweep order of the solve in progress
   unsigned spin_limit = 0;     // bounded waits of the sweep kernel (0: the default)
   int dbg_skip_cta = -1;       // fault injection: this CTA skips one barrier arrival
+  cudaEvent_t kev[2] = {nullptr, nullptr};  // brackets of each sweep launch in hq_solve
   void* wv64 = nullptr;        // per-state weights (w'', v'') in FP64 (double2, layer-ranked)
   void* wv32 = nullptr;        // the same in FP32 (float2)
   // instance

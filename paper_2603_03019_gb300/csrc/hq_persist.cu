@@ -823,14 +823,22 @@ __global__ void __launch_bounds__(256) k_iter_sums(SumArgs a) {
   }
 }
 
-// dst[q][n] = sum over warps (in order) of part[w][n][q]; dst has stride HQ_MAXN + 1
-__global__ void k_iter_sums_fold(int N, int nwarps, const double* part, double* dst) {
-  const int i = threadIdx.x;
-  if (i >= 4 * (N + 1)) return;
+// dst[q][n] = sum over warps of part[w][n][q]; dst has stride HQ_MAXN + 1.  One CTA per
+// output: thread t sums warps t, t + 256, ... in order, then a fixed halving tree
+// (the same order on every run).
+__global__ void __launch_bounds__(256) k_iter_sums_fold(int N, int nwarps, const double* part, double* dst) {
+  __shared__ double red[256];
+  const int i = blockIdx.x;
   const int q = i / (N + 1), n = i % (N + 1);
   double v = 0.0;
-  for (int w = 0; w < nwarps; w++) v += part[((size_t)w * (HQ_MAXN + 1) + n) * 4 + q];
-  dst[q * (HQ_MAXN + 1) + n] = v;
+  for (int w = threadIdx.x; w < nwarps; w += 256) v += part[((size_t)w * (HQ_MAXN + 1) + n) * 4 + q];
+  red[threadIdx.x] = v;
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) dst[q * (HQ_MAXN + 1) + n] = red[0];
 }
 
 // w''(l) = sum_{u idle in l} lambda_u(l) mu_{l+u} r_{l+u} (the upward rates are the
@@ -869,11 +877,9 @@ __global__ void __launch_bounds__(256) k_weights(WeightArgs a, int64_t Sp) {
       const uint32_t lo = y & ((1u << L) - 1u), hi = y >> L;
       return __ldg(a.RL + lo) + __ldg(a.RH + (size_t)hi * (L + 1) + __popc(lo));
     };
-    auto mu_of = [&](uint32_t y) -> double {
-      double m = 0.0;
-      for (; y; y &= y - 1u) m += snu[__ffs(y) - 1];
-      return m;
-    };
+    // mu of a neighbour: mu(x) plus or minus one unit's rate
+    double mux = 0.0;
+    for (uint32_t y = x; y; y &= y - 1u) mux += snu[__ffs(y) - 1];
     if (n < N) {
       for (int u = 0; u < N; u++) {
         if ((x >> u) & 1u) continue;
@@ -882,7 +888,7 @@ __global__ void __launch_bounds__(256) k_weights(WeightArgs a, int64_t Sp) {
         const int slot = __popc(x & ((1u << u) - 1u));
         const double t = a.T[a.toff[n + 1] + (int64_t)ry * a.tw[n + 1] + slot];
         const double ryv = a.r[a.off[n + 1] + ry];
-        wu += t * mu_of(y) * ryv;
+        wu += t * (mux + snu[u]) * ryv;
       }
     }
     if (n > 0) {
@@ -890,7 +896,7 @@ __global__ void __launch_bounds__(256) k_weights(WeightArgs a, int64_t Sp) {
         if (!((x >> u) & 1u)) continue;
         const uint32_t y = x ^ (1u << u);
         const uint32_t ry = rank(y);
-        wd += snu[u] * mu_of(y) * a.r[a.off[n - 1] + ry];
+        wd += snu[u] * (mux - snu[u]) * a.r[a.off[n - 1] + ry];
       }
     }
   }
@@ -1094,7 +1100,7 @@ int hq_iter_sums(hq_solver* h, int prec, const void* p, double* dst) {
   else if (prec == HQ_PREC_DF64) k_iter_sums<PolDF><<<grid, 256, 0, h->stream>>>(a);
   else k_iter_sums<PolF32><<<grid, 256, 0, h->stream>>>(a);
   HQ_LAUNCHED();
-  k_iter_sums_fold<<<1, 128, 0, h->stream>>>(h->N, (int)warps, h->partials, dst);
+  k_iter_sums_fold<<<4 * (h->N + 1), 256, 0, h->stream>>>(h->N, (int)warps, h->partials, dst);
   HQ_LAUNCHED();
   return HQ_OK;
 }

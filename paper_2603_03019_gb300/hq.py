@@ -44,7 +44,9 @@ class hq_stats(ctypes.Structure):
                 ("final_step", ctypes.c_double), ("final_residual", ctypes.c_double),
                 ("ms_total", ctypes.c_double), ("ms_table", ctypes.c_double),
                 ("state_updates", ctypes.c_double), ("warm_used", ctypes.c_int),
-                ("ir_bases", ctypes.c_int), ("omega", ctypes.c_double), ("reserved", ctypes.c_int * 2)]
+                ("ir_bases", ctypes.c_int), ("omega", ctypes.c_double),
+                ("ms_sweeps_fp32", ctypes.c_double), ("ms_sweeps_hi", ctypes.c_double),
+                ("reserved", ctypes.c_int * 2)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
