@@ -90,6 +90,9 @@ def parse():
     ap.add_argument("--sweeps", type=int, default=2)
     ap.add_argument("--repeats", type=int, default=3,
                     help="solves per time-to-tolerance arm (the median is reported)")
+    ap.add_argument("--fp-rate", action="store_true",
+                    help="FP64 and FP32 FMA issue rates of this GPU (the FP64 ceiling of the "
+                         "FP64 sweep), one JSON line each, with the SM clocks sampled meanwhile")
     ap.add_argument("--order", default="redblack", choices=["ascending", "redblack"],
                     help="sweep order of the solve (--profile and the headline path)")
     return ap.parse_args()
@@ -678,8 +681,43 @@ def run_warmstart(args):
     return 0
 
 
+def run_fp_rate(args):
+    """Build and run the FMA-rate microbenchmark (microbench/fp_rate.cu) with the clocks
+    sampled during it; prints its lines with the median SM clock and the FP64 rate per
+    SM per cycle at that clock."""
+    src = os.path.join(ROOT, "paper_2603_03019_gb300", "microbench", "fp_rate.cu")
+    out_dir = os.path.join(ROOT, "paper_2603_03019_gb300", "_build")
+    os.makedirs(out_dir, exist_ok=True)
+    exe = os.path.join(out_dir, "fp_rate")
+    nvcc = os.environ.get("NVCC") or "nvcc"
+    subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-O3", src, "-o", exe], check=True)
+    clocks = ClockSampler(0)
+    clocks.start()
+    r = subprocess.run([exe, "20000", "40", "4"], capture_output=True, text=True)
+    clk = clocks.stop()
+    if r.returncode != 0:
+        print(json.dumps({"fp_rate": "failed", "rc": r.returncode, "stderr": r.stderr[-400:]}))
+        return r.returncode
+    nsm = None
+    try:
+        import torch
+
+        nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    except Exception:
+        pass
+    for ln in r.stdout.splitlines():
+        d = json.loads(ln)
+        d["clocks"] = clk
+        if nsm and clk.get("sm_mhz"):
+            d["fma_per_sm_per_clk"] = round(d["fma_per_s"] / (nsm * clk["sm_mhz"] * 1e6), 3)
+        print(json.dumps(d))
+    return 0
+
+
 def main():
     args = parse()
+    if args.fp_rate:
+        return run_fp_rate(args)
     if args.warmstart:
         return run_warmstart(args)
     if args.batch:

@@ -246,8 +246,10 @@ __device__ __forceinline__ double2 ld_vec(const double2* p) { return __ldcs(p); 
 // neighbours by table slot (low units, then high units: slot W + j), idle neighbours by
 // unit (low, then high).  tv: the state's table record; h: its high-part neighbours (busy
 // units first, as the warp's list); lx: its low-part positions and idle units.
-// The low- and high-part sums run as separate chains (then low + high), which halves the
-// dependent FMA chain of a state; inside each part the order is by slot / by unit.
+// FP32 and DF64: the low- and high-part sums run as separate chains (then low + high),
+// which halves the dependent FMA chain of a state.  FP64, whose sweep is bound by the
+// FP64 pipe on this chip, keeps one chain per sum (two adds fewer per state).  Inside
+// each part the order is by slot / by unit.
 template <int W, class V, int kHP, int kNV>
 __device__ __forceinline__ void inflows(typename V::T& U, typename V::T& D, const typename Vec<V>::VT* tv,
                                         const typename V::T* h, const uint4& lx, const typename V::T* sdn,
@@ -255,7 +257,10 @@ __device__ __forceinline__ void inflows(typename V::T& U, typename V::T& D, cons
                                         const typename V::T* nu, const typename V::T* hnu) {
   typedef typename V::T T;
   constexpr int kMaxSlot = kNV * Vec<V>::kPer;
-  T Ul = V::zero(), Uh = V::zero(), Dl = V::zero(), Dh = V::zero();
+  constexpr bool kOne = V::kind == HQ_PREC_FP64;
+  T Ul = V::zero(), Uh0 = V::zero(), Dl = V::zero(), Dh0 = V::zero();
+  T& Uh = kOne ? Ul : Uh0;
+  T& Dh = kOne ? Dl : Dh0;
 #pragma unroll
   for (int k = 0; k < W; k++) {
     const uint32_t pos = (lx_word(lx, k >> 2) >> (8 * (k & 3))) & 0xffu;
@@ -279,8 +284,13 @@ __device__ __forceinline__ void inflows(typename V::T& U, typename V::T& D, cons
     if (j < nbh) continue;
     V::fma_acc(Dh, h[j], hnu[j]);
   }
-  U = V::add(V::norm(Ul), V::norm(Uh));
-  D = V::add(V::norm(Dl), V::norm(Dh));
+  if constexpr (kOne) {
+    U = Ul;
+    D = Dl;
+  } else {
+    U = V::add(V::norm(Ul), V::norm(Uh));
+    D = V::add(V::norm(Dl), V::norm(Dh));
+  }
 }
 
 // One item's loads, held in registers from issue to compute.
@@ -493,7 +503,6 @@ __device__ __forceinline__ void run_items(Smem<V, kWarps, kHP>& s, const SweepAr
 #undef HQ_INFLOWS
       default: break;
     }
-    const T A = V::mul(U, ld.rv), B = V::mul(D, ld.rv);
     const T c1 = s.c1[n], c2 = s.c2[n];
     if constexpr (kMode == 3) {
       // Eq. (1) at this state: out = P (lambda + mu_m), in = P-weighted inflows from its
@@ -509,14 +518,15 @@ __device__ __forceinline__ void run_items(Smem<V, kWarps, kHP>& s, const SweepAr
       // base pass: rho0 = c1^0 A0 + c2^0 B0 - p0 (FP64 here), stored in FP32
       if (act) {
         float* outn = a.out + s.off[n] + ir.rk;
-        const double A0 = V::to_d(A), B0 = V::to_d(B);
+        const double A0 = V::to_d(U) * V::to_d(ld.rv), B0 = V::to_d(D) * V::to_d(ld.rv);
         const double rho0 = V::to_d(c1) * A0 + V::to_d(c2) * B0 - V::to_d(ld.po);
         outn[0] = (float)rho0;
         outn[a.Sp] = (float)A0;
         outn[2 * a.Sp] = (float)B0;
       }
     } else {
-      T pn = V::add(V::mul(c1, A), V::mul(c2, B));
+      // c1 A + c2 B with A = r U, B = r D
+      T pn = V::mul(ld.rv, V::add(V::mul(c1, U), V::mul(c2, D)));
       if constexpr (kMode == 1)
         pn = V::add(V::add(ld.q0, V::add(V::mul(s.d1[n], ld.q1), V::mul(s.d2[n], ld.q2))), pn);
       if (relax) pn = V::add(ld.po, V::mul(om, V::sub(pn, ld.po)));
@@ -907,16 +917,20 @@ __global__ void __launch_bounds__(256) k_weights(WeightArgs a, int64_t Sp) {
 // ---- launch ---------------------------------------------------------------------------------
 
 constexpr int kSweepThreads = 512;
+constexpr int kSweepThreadsWide = 384;
 
-// One CTA of 512 threads per SM (16 warps, up to 128 registers) for every precision:
-// measured on the FP32 sweep at N=24, 384 threads (with two items in flight per warp or
-// one) and 768 threads (spilling) were slower.
-int sweep_threads(int, int) { return kSweepThreads; }
+// One CTA per SM.  FP32 sweeps: 512 threads (16 warps, up to 128 registers); measured at
+// N=24, 384 threads (with two items in flight per warp or one) and 768 threads (spilling)
+// were slower.  FP64 and DF64 sweeps, whose wider values spill at 128 registers: 384
+// threads (12 warps, up to 168 registers); measured at N=24 against 512 and 256, DF64
+// 1.36 vs 1.63 and 1.80 ms per red-black sweep, FP64 1.98 vs 2.00 and 2.21 ms.
+int sweep_threads(int, int kind) { return kind == HQ_PREC_FP32 ? kSweepThreads : kSweepThreadsWide; }
 
 template <class V, bool kIR>
 const void* sweep_fn(int H) {
-  if (H <= 14) return (const void*)k_sweep<V, kIR, 14, kSweepThreads>;
-  return (const void*)k_sweep<V, kIR, 18, kSweepThreads>;
+  constexpr int kT = V::kind == HQ_PREC_FP32 ? kSweepThreads : kSweepThreadsWide;
+  if (H <= 14) return (const void*)k_sweep<V, kIR, 14, kT>;
+  return (const void*)k_sweep<V, kIR, 18, kT>;
 }
 
 int g_nsm = 0;
