@@ -142,7 +142,10 @@ typedef struct hq_solver hq_solver;
  * every 8 sweeps, max 100000 sweeps, omega 1, cold start. */
 void hq_default_opts(hq_opts* opts);
 
-/* Allocate a solver for N units (1..28), J nodes (>= 1) and a queue mode
+/* The model of Section 2.1 (N units with their own service rates, J demand nodes with
+ * preference lists, first-idle dispatch) in the loss form, the finite-buffer form of
+ * Section 2.2's finite-buffer reformulation or the infinite-queue form of its Remark.
+ * Allocate a solver for N units (1..28), J nodes (>= 1) and a queue mode
  * (capacity_C >= 1 iff HQ_FINITE, ignored otherwise) on the current device.
  * stream: a cudaStream_t, or NULL for the default stream.  Allocates every device
  * buffer the solve needs: about 14 N 2^N bytes for the upward-rate table in FP64,
@@ -180,18 +183,27 @@ int hq_get_layer_marginals(hq_solver* h, double* pn, double* queue_tail, int mem
 /* Conditional probabilities p_n(B) (each layer sums to 1), y-order, 2^N values. */
 int hq_get_conditional(hq_solver* h, double* p, int mem);
 
-/* rho_i: fraction of time unit i is busy (queued states count as busy), N values. */
+/* rho_i: fraction of time unit i is busy (queued states count as busy), N values:
+ * the unit utilisation of Section 5.5 (its Table of utilisation errors), the sum of
+ * P{B} over the states with unit i busy plus the queue's mass.  The throughput
+ * identity sum_i nu_i rho_i = carried load holds. */
 int hq_get_utilisation(hq_solver* h, double* rho, int mem);
 
-/* R[j*N + i]: probability that a call from node j is served by unit i (J x N).
+/* Response pattern: the Introduction names it among the measures the stationary
+ * distribution yields but does not define it; this is the standard hypercube
+ * definition (first-idle dispatch of Section 2.1 applied to P{B}).
+ * R[j*N + i]: probability that a call from node j is served by unit i (J x N).
  * Calls that wait are served by the unit that frees first: unit i w.p.
  * nu_i / sum nu.  Rows sum to 1 - P(call lost). */
 int hq_get_response_pattern(hq_solver* h, double* R, int mem);
 
-/* W[i*J + j] = lambda_j R_ji / nu_i: fraction of time unit i serves node j (N x J). */
+/* Unit workload by node (named in the Introduction, not defined in the paper; the
+ * standard hypercube split of rho_i over the nodes):
+ * W[i*J + j] = lambda_j R_ji / nu_i: fraction of time unit i serves node j (N x J). */
 int hq_get_workload(hq_solver* h, double* W, int mem);
 
-/* Scalars: out[0] throughput sum_i nu_i rho_i, out[1] P(call lost),
+/* Scalars derived from P (not in the paper except the residual, which measures Eq. (1)
+ * of Section 2.1 on the returned P): out[0] throughput sum_i nu_i rho_i, out[1] P(call lost),
  * out[2] P(call waits), out[3] relative balance residual of the returned P,
  * out[4] mean number of busy units. 5 doubles, host memory. */
 int hq_get_summary(hq_solver* h, double* out5);
@@ -223,10 +235,11 @@ int hq_profile_sweep(hq_solver* h, int precision, int sweeps, float* ms_out);
  * written (at most 64 are recorded), or a negative hq_status. */
 int hq_profile_phases(hq_solver* h, double* us_out, int max_out);
 
-/* Algorithmic HBM bytes of one outer iteration in `precision`: per state of
- * layers 1..N-1, its n table entries, r_m, its state mask, one read and one write
- * of p (neighbour layers are L2-resident and not counted); HQ_PREC_FP32_IR: an FP32
- * correction sweep, which also reads six FP32 base terms per state.  Host double. */
+/* Algorithmic HBM bytes of one outer iteration (Algorithm 1) in `precision`: per
+ * state of layers 1..N-1, its n table entries, r_m, one read and one write of p
+ * (neighbour layers are L2-resident and not counted): (n + 3) values per state;
+ * HQ_PREC_FP32_IR: an FP32 correction sweep, which also reads three FP32 base terms
+ * per state (12 bytes).  Not in the paper: a measurement aid.  Host double. */
 double hq_sweep_bytes(const hq_solver* h, int precision);
 
 /* Upward-rate table without any device allocation.  The paper has no
@@ -346,7 +359,11 @@ int hq_mlp_predict(hq_solver* h, hq_mlp* m, double* q, double* pn, double* rho, 
 int hq_attach_mlp(hq_solver* h, hq_mlp* m);
 void hq_mlp_destroy(hq_mlp* m);
 
+/* Release a solver and every device buffer it holds (the model of hq_create; not in
+ * the paper).  NULL is ignored.  A model attached by hq_attach_mlp is not freed. */
 void hq_destroy(hq_solver* h);
+/* Library housekeeping, not in the paper: a static text for an hq_status code, and the
+ * calling thread's message for its last failed call ("" if none). */
 const char* hq_strerror(int code);
 const char* hq_last_error(void);
 
