@@ -111,3 +111,92 @@ def test_product_form_special_cases():
     erl = np.array([2.0 ** n / math.factorial(n) for n in range(N + 1)])
     assert np.allclose(P, erl / erl.sum(), atol=1e-15)
     assert np.allclose(rho, np.full(N, (P * np.arange(N + 1)).sum() / N), atol=1e-15)
+
+
+# ---- pins of the BF16 rounding points, independent of the oracle's own arithmetic ------
+
+def _flat(W1, b1, W2, b2, W3, b3):
+    return np.concatenate([np.ravel(W1), b1, np.ravel(W2), b2, W3, [b3]]).astype(np.float64)
+
+
+def test_bf16_points_are_no_ops_on_dyadic_values():
+    """Small integers and halves everywhere: every input, weight, activation and error
+    signal is exact in BF16 (8 significant bits) and FP32, so rounding at the BF16
+    points must change nothing: forward, loss and gradient agree with the exact FP64
+    network to 1e-12 (in fact exactly)."""
+    r = np.random.default_rng(17)
+    H, B = 16, 4
+    W1 = r.integers(-1, 2, (mlp.F, H)).astype(np.float64)       # z1 integers in [-18, 19]
+    b1 = r.integers(0, 2, H).astype(np.float64)
+    W2 = np.zeros((H, H))
+    for c in range(H):                                          # two entries per column
+        rows = r.choice(H, 2, replace=False)
+        W2[rows, c] = r.choice([-1.0, -0.5, 0.5, 1.0], 2)       # |z2| <= 38, step 1/2
+    b2 = r.integers(0, 2, H).astype(np.float64)
+    W3 = r.choice([-1.0, -0.5, 0.0, 0.5, 1.0], H)
+    b3 = 0.25
+    X = r.integers(0, 3, (B, mlp.F)).astype(np.float64)
+    w = _flat(W1, b1, W2, b2, W3, b3)
+    y_ex, c_ex = mlp.forward(w, X, H, False)
+    # targets one small integer away from the output: e, dy = 2 e / B = e / 2 and
+    # dz2 = dy W3 are dyadic with a few bits
+    t = y_ex - r.integers(-2, 3, B)
+    y_bf, c_bf = mlp.forward(w, X, H, True)
+    for k in ("a1", "a2", "W2"):
+        assert np.array_equal(mlp.bf16(c_ex[k]), c_ex[k]), k    # the values are BF16-exact
+    assert np.max(np.abs(y_bf - y_ex)) <= 1e-12
+    l_ex, g_ex = mlp.loss_and_grad(w, X, t, H, False)
+    l_bf, g_bf = mlp.loss_and_grad(w, X, t, H, True)
+    assert abs(l_bf - l_ex) <= 1e-12
+    assert np.max(np.abs(g_bf - g_ex)) <= 1e-12
+    assert np.count_nonzero(g_ex) > H                           # a non-trivial gradient
+
+
+def test_bf16_points_two_hidden_units_by_hand():
+    """Two hidden units, one input row, every BF16 rounding point deciding something.
+    Worked by hand (BF16 keeps 8 significant bits: spacing 2^-7 on [1, 2), 2^-6 on
+    [2, 4); ties go to the even significand):
+      z1 = x W1 + b1 = [1 + 2^-8, 1]            (FP32, exact)
+      a1 = bf16(relu z1) = [1, 1]               (1 + 2^-8 is a tie: down to even 1)
+      bf16(W2) = [[1 + 2^-7, 0], [0, 3]]        (1 + 3 2^-9 is 3/4 of a step: up)
+      z2 + b2 = [1 + 2^-7 + 2^-9, 3.5]
+      a2 = [1 + 2^-7, 3.5]                      (a quarter step: down)
+      y = a2 . W3 + b3 = (1 + 2^-7)(1 + 2^-8 + 2^-10) - 3.5 + 0.25
+        = -2.25 + 2^-7 + 2^-8 + 2^-10 + 2^-15 + 2^-17
+    The target is y - 2^-4, so e = 2^-4, loss = 2^-8, dy = 2 e = 2^-3 (B = 1):
+      dz2 = bf16(dy W3) = bf16([2^-3 (1 + 2^-8 + 2^-10), -2^-3])
+          = [2^-3 (1 + 2^-7), -2^-3]           (0.625 of a step: up)
+      dW3 = dy a2 = [2^-3 (1 + 2^-7), 3.5 2^-3], db3 = 2^-3
+      dW2 = a1^T dz2 (both rows [2^-3 (1 + 2^-7), -2^-3]), db2 = dz2
+      da1 = dz2 bf16(W2)^T = [2^-3 (1 + 2^-7)^2, -3 2^-3] = dz1 (a1 > 0)
+      dW1 = x^T dz1 (row 0 only), db1 = dz1."""
+    H = 2
+    W1 = np.zeros((mlp.F, H))
+    W1[0] = [1 + 2.0 ** -8, 1.0]
+    b1 = np.zeros(H)
+    W2 = np.array([[1 + 3 * 2.0 ** -9, 0.0], [0.0, 3.0]])
+    b2 = np.array([2.0 ** -9, 0.5])
+    W3 = np.array([1 + 2.0 ** -8 + 2.0 ** -10, -1.0])
+    b3 = 0.25
+    X = np.zeros((1, mlp.F))
+    X[0, 0] = 1.0
+    w = _flat(W1, b1, W2, b2, W3, b3)
+    y_hand = -2.25 + 2.0 ** -7 + 2.0 ** -8 + 2.0 ** -10 + 2.0 ** -15 + 2.0 ** -17
+    y, c = mlp.forward(w, X, H, True)
+    assert y[0] == y_hand
+    assert np.array_equal(c["a1"], [[1.0, 1.0]])
+    assert np.array_equal(c["W2"], [[1 + 2.0 ** -7, 0.0], [0.0, 3.0]])
+    assert np.array_equal(c["a2"], [[1 + 2.0 ** -7, 3.5]])
+    t = np.array([y_hand - 2.0 ** -4])
+    loss, g = mlp.loss_and_grad(w, X, t, H, True)
+    assert loss == 2.0 ** -8
+    s = 2.0 ** -3
+    u = 1 + 2.0 ** -7
+    dz1 = [s * u * u, -3 * s]
+    dW1 = np.zeros((mlp.F, H))
+    dW1[0] = dz1
+    want = _flat(dW1, dz1, [[s * u, -s], [s * u, -s]], [s * u, -s], [s * u, 3.5 * s], s)
+    assert np.array_equal(g, want), np.nonzero(g != want)
+    # the exact network differs at every step (the rounding points are not no-ops here)
+    y_ex = mlp.forward(w, X, H, False)[0]
+    assert abs(y_ex[0] - y_hand) > 2.0 ** -10
