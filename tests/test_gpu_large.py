@@ -16,6 +16,7 @@ max-abs; the same path run to a 1e-12 residual meets 1e-10 everywhere.
 N=20, J=500, loss system, loads 0.3 / 0.6 / 0.9: full oracle solves in the test (the
 oracle's OpenMP build), compared element by element with both refinement forms.
 """
+import math
 import os
 
 import numpy as np
@@ -116,3 +117,64 @@ def test_n20_loads_against_oracle(gpu_lib, n20_oracle, load, prec, order):
     assert np.max(np.abs(W - r["W"])) < 1e-10
     assert abs(summ["throughput"] - r["throughput"]) < 1e-10
     assert summ["residual"] <= 1e-12
+
+
+def test_n26_sampled(gpu_lib):
+    """N=26 (2^26 = 67M states, 0.87 G table entries), J=1000, the benchmark workload's
+    shape, solved with the benchmark's options: sampled table entries against Eq. (3)
+    evaluated by the oracle's dispatch rule, sampled global balance of Eq. (1) with the
+    oracle's rates, and the invariants.  The table is read on the device and sampled
+    there (7 GB in FP64)."""
+    import torch
+
+    N = 26
+    inst = I.large_infinite_n24(3001, N=N)
+    s = hq.Solver.for_instance(inst)
+    rc, st = s.solve(tol=1e-10, precision="fp32+ir", omega=-1.0, order="redblack")
+    assert rc == hq.HQ_OK and st["final_residual"] <= 1e-10, st
+    P = s.stationary()
+    pn, tail = s.layer_marginals()
+    rho, R = s.utilisation(), s.response_pattern()
+    summ = s.summary()
+    info = hq.hq_get_info(s.h)
+    dev = torch.device("cuda", 0)
+    T = torch.empty(int(info[5]), dtype=torch.float64, device=dev)
+    masks = torch.empty(1 << N, dtype=torch.int32, device=dev)
+    hq.hq_get_table(s.h, T, masks)
+    s.close()
+    rng = np.random.default_rng(26)
+    sizes = [math.comb(N, n) for n in range(N + 1)]
+    off = np.concatenate([[0], np.cumsum(sizes)])
+    toff = np.concatenate([[0], np.cumsum([n * sizes[n] for n in range(N + 1)])])
+    ns = rng.integers(1, N + 1, 400)
+    ks = np.array([int(rng.integers(0, sizes[n])) for n in ns])
+    ms = masks[torch.as_tensor(off[ns] + ks, device=dev)].cpu().numpy().astype(np.int64) & 0xFFFFFFFF
+    slots = np.array([int(rng.integers(0, n)) for n in ns])
+    got = T[torch.as_tensor(toff[ns] + slots * np.array([sizes[n] for n in ns]) + ks, device=dev)].cpu().numpy()
+    src, units = [], []
+    for m, sl in zip(ms, slots):
+        busy = [u for u in range(N) if (m >> u) & 1]
+        src.append(m & ~(1 << busy[sl]))
+        units.append(busy[sl])
+    want = oracle.dispatch_rates(inst, src=np.array(src, dtype=np.uint64), u=np.array(units, dtype=np.int32))
+    assert np.all(np.abs(got - want) <= 1e-13 * np.maximum(1.0, want))
+    del T, masks
+    # sampled global balance with the oracle's dispatch rule
+    B = rng.integers(0, 1 << N, 1500).astype(np.uint64)
+    B[:3] = [0, (1 << N) - 1, (1 << N) - 2]
+    Bi = B.astype(np.int64)
+    nb = np.stack([P[Bi ^ (1 << u)] for u in range(N)], axis=1)
+    lam = inst.lam
+    pq1 = P[-1] * lam / inst.nu.sum()
+    out, inn = oracle.sampled_balance(inst, B, P[Bi], nb, pq1)
+    y = torch.arange(1 << N, dtype=torch.int64, device=dev)
+    mu = torch.zeros(1 << N, dtype=torch.float64, device=dev)
+    for u in range(N):
+        mu += ((y >> u) & 1).double() * float(inst.nu[u])
+    den = float(torch.max(torch.as_tensor(P, device=dev) * (lam + mu)))
+    assert np.max(np.abs(out - inn)) / den < 1e-10
+    assert abs(P.sum() + tail - 1.0) < 1e-12
+    assert abs(pn.sum() + tail - 1.0) < 1e-12
+    assert np.allclose(R.sum(axis=1), 1.0, rtol=0, atol=1e-10)
+    bound = (1 << (N - 1)) * summ["residual"] * den
+    assert np.max(np.abs(inst.lam_j @ R - inst.nu * rho)) <= bound

@@ -168,7 +168,10 @@ def test_trained_network_gains(gpu_lib):
     without it: an estimate of every unit's utilisation in one forward pass that is on
     average less than half as far from the solved one as what the paper's uniform start
     implies (q_i(n) = n/N), and a solve from the learned start that reaches the same
-    solution at about the cost of a cold one (its two probe sweeps and the fallback)."""
+    solution at about the cost of a cold one.  It does not shorten the solve: the
+    iteration's rate, not its start, sets the sweep count, and the residual test (two
+    FP64 residual evaluations) keeps the learned start only where it is closer than the
+    uniform one."""
     m = hq.load_warmstart_model()
     cold_total, warm_total, err_net, err_uniform = 0, 0, [], []
     for N, seed in ((16, 777001), (18, 777002), (20, 777003)):
