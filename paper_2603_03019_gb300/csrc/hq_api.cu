@@ -64,7 +64,7 @@ static void free_all(hq_solver* h) {
                   h->b64.T, h->b64.r, h->b64.p, h->b64.nu, h->bdf.T, h->bdf.r, h->bdf.p, h->bdf.nu,
                   h->b32.T, h->b32.r, h->b32.p, h->b32.nu, h->ab, h->partials, h->sc, h->dflag,
                   h->P, h->pn, h->rho, h->R, h->W, h->summary, h->pcond, h->ir_base, h->ir, h->ir_part,
-                  h->wv64, h->wv32, h->sitems[0], h->sitems[1], h->sblocks[0], h->sblocks[1],
+                  h->wv64, h->wv32, h->mutab, h->sitems[0], h->sitems[1], h->sblocks[0], h->sblocks[1],
                   h->sperm[0], h->sperm[1]};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -173,6 +173,7 @@ extern "C" int hq_create(int N, int J, int mode, int capacity_C, void* stream, h
   HQ_TRY(dalloc(h, &h->ir, SP * 12));
   HQ_TRY(dalloc(h, (double2**)&h->wv64, SP * 16));
   HQ_TRY(dalloc(h, (float2**)&h->wv32, SP * 8));
+  HQ_TRY(dalloc(h, &h->mutab, (((int64_t)1 << h->L) + ((int64_t)1 << h->H)) * 8));
   HQ_TRY(dalloc(h, (double**)&h->b64.nu, (int64_t)HQ_MAXN * 8));
   HQ_TRY(dalloc(h, (float2**)&h->bdf.nu, (int64_t)HQ_MAXN * 8));
   HQ_TRY(dalloc(h, (float**)&h->b32.nu, (int64_t)HQ_MAXN * 4));

@@ -268,6 +268,7 @@ struct hq_solver {
   cudaEvent_t kev[2] = {nullptr, nullptr};  // brackets of each sweep launch in hq_solve
   void* wv64 = nullptr;        // per-state weights (w'', v'') in FP64 (double2, layer-ranked)
   void* wv32 = nullptr;        // the same in FP32 (float2)
+  double* mutab = nullptr;     // mu of a low part (2^L entries), then of a high part (2^H)
   // instance
   double* lam_j = nullptr;     // J
   double* nu = nullptr;        // N

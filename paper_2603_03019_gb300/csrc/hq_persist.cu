@@ -781,16 +781,15 @@ struct SumArgs {
   const uint32_t* masks;
   const void* p;
   const double2* wv;   // FP64 weights
-  const double* nu;
+  const double* mulo;  // mu of each low part (2^L), then mu of each high part (2^H)
+  const double* muhi;
   double* part;        // [warps][HQ_MAXN + 1][4]
 };
 
 template <class V>
 __global__ void __launch_bounds__(256) k_iter_sums(SumArgs a) {
-  __shared__ double snu[HQ_MAXN];
-  if ((int)threadIdx.x < a.N) snu[threadIdx.x] = a.nu[threadIdx.x];
-  __syncthreads();
   const int lane = threadIdx.x & 31;
+  const uint32_t lomask = (1u << a.L) - 1u;
   const int64_t chunks = a.off[a.N + 1] >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -817,8 +816,8 @@ __global__ void __launch_bounds__(256) k_iter_sums(SumArgs a) {
     }
     if (g - a.off[n] < a.lsize[n]) {
       const double pv = V::to_d(p[g]);
-      double mu = 0.0;
-      for (uint32_t y = a.masks[g]; y; y &= y - 1u) mu += snu[__ffs(y) - 1];
+      const uint32_t x = a.masks[g];
+      const double mu = __ldg(a.mulo + (x & lomask)) + __ldg(a.muhi + (x >> a.L));
       const double2 wq = a.wv[g];
       acc[0] += pv;
       acc[1] += pv * mu;
@@ -866,10 +865,28 @@ struct WeightArgs {
   const double* T;
   const double* r;
   const double* nu;
+  const double* mulo;
+  const double* muhi;
   double lam, lam_full;
   double2* w64;
   float2* w32;
 };
+
+// mu of every low part (sum of nu over its busy units, in unit order) and of every high
+// part: mu(x) = mulo[x & (2^L - 1)] + muhi[x >> L]
+__global__ void k_mu_tables(int L, int H, const double* nu, double* mulo, double* muhi) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nlo = (int64_t)1 << L, nhi = (int64_t)1 << H;
+  if (i < nlo) {
+    double m = 0.0;
+    for (uint32_t y = (uint32_t)i; y; y &= y - 1u) m += nu[__ffs(y) - 1];
+    mulo[i] = m;
+  } else if (i < nlo + nhi) {
+    double m = 0.0;
+    for (uint32_t y = (uint32_t)(i - nlo); y; y &= y - 1u) m += nu[L + __ffs(y) - 1];
+    muhi[i - nlo] = m;
+  }
+}
 
 __global__ void __launch_bounds__(256) k_weights(WeightArgs a, int64_t Sp) {
   __shared__ double snu[HQ_MAXN];
@@ -888,8 +905,7 @@ __global__ void __launch_bounds__(256) k_weights(WeightArgs a, int64_t Sp) {
       return __ldg(a.RL + lo) + __ldg(a.RH + (size_t)hi * (L + 1) + __popc(lo));
     };
     // mu of a neighbour: mu(x) plus or minus one unit's rate
-    double mux = 0.0;
-    for (uint32_t y = x; y; y &= y - 1u) mux += snu[__ffs(y) - 1];
+    const double mux = __ldg(a.mulo + (x & ((1u << L) - 1u))) + __ldg(a.muhi + (x >> L));
     if (n < N) {
       for (int u = 0; u < N; u++) {
         if ((x >> u) & 1u) continue;
@@ -1099,7 +1115,8 @@ int hq_iter_sums(hq_solver* h, int prec, const void* p, double* dst) {
   a.masks = h->masks;
   a.p = p;
   a.wv = (const double2*)h->wv64;
-  a.nu = h->nu;
+  a.mulo = h->mutab;
+  a.muhi = h->mutab + ((int64_t)1 << h->L);
   a.part = h->partials;
   // 8 warps per CTA; at most partials_len / (4 (HQ_MAXN + 1)) warps
   const int64_t chunks = h->Sp >> 5;
@@ -1142,6 +1159,14 @@ int hq_build_weights(hq_solver* h) {
   a.lam_full = h->mode == HQ_LOSS ? 0.0 : h->lam;
   a.w64 = (double2*)h->wv64;
   a.w32 = (float2*)h->wv32;
+  a.mulo = h->mutab;
+  a.muhi = h->mutab + ((int64_t)1 << h->L);
+  {
+    const int64_t nt = ((int64_t)1 << h->L) + ((int64_t)1 << h->H);
+    k_mu_tables<<<(unsigned)((nt + 255) / 256), 256, 0, h->stream>>>(h->L, h->H, h->nu, h->mutab,
+                                                                    h->mutab + ((int64_t)1 << h->L));
+    HQ_LAUNCHED();
+  }
   k_weights<<<(unsigned)((h->Sp + 255) / 256), 256, 0, h->stream>>>(a, h->Sp);
   HQ_LAUNCHED();
   return HQ_OK;
