@@ -90,6 +90,10 @@ def parse():
     ap.add_argument("--sweeps", type=int, default=2)
     ap.add_argument("--repeats", type=int, default=3,
                     help="solves per time-to-tolerance arm (the median is reported)")
+    ap.add_argument("--des", action="store_true",
+                    help="the service-distribution check of Section 5.5 on the GPU simulation: "
+                         "MPRE of MRT and utilisation against the hypercube solution, 15 cases per "
+                         "distribution (one JSON line)")
     ap.add_argument("--fp-rate", action="store_true",
                     help="FP64 and FP32 FMA issue rates of this GPU (the FP64 ceiling of the "
                          "FP64 sweep), one JSON line each, with the SM clocks sampled meanwhile")
@@ -714,8 +718,74 @@ def run_fp_rate(args):
     return 0
 
 
+def run_des(args):
+    """Section 5.5's check on synthetic inputs: for N in {8, 10, 12} and load in
+    {0.1, 0.3, 0.5, 0.7, 0.9} (15 cases) and each service distribution, the GPU
+    simulation's mean response time and unit utilisations against the exact loss-system
+    solution (GPU, FP64, 1e-12 residual): MPRE in per cent as in the paper's Eq. for
+    MPRE.  Per case 1,280 replications of 16,000 calls (400 not counted): the same 2e7
+    calls as the paper's 20 replications of 10^6.  Beside it the oracle's simulation on
+    one host core, timed on a bounded sample."""
+    import torch
+
+    import oracle
+    from paper_2603_03019_gb300 import hq
+
+    hq.load()
+    kinds = ["exponential", "lognormal", "gamma5", "gamma05", "uniform"]
+    reps, arr, warm = 1280, 16_000, 400
+    cases = [(N, ld) for N in (8, 10, 12) for ld in (0.1, 0.3, 0.5, 0.7, 0.9)]
+    exact = {}
+    for N, ld in cases:
+        inst = I.des_instance(6000 + N, N=N, load=ld)
+        tt = I.travel_times(inst)
+        s = hq.Solver.for_instance(inst)
+        s.solve(tol=1e-12, precision="fp64")
+        R = s.response_pattern()
+        served = R * inst.lam_j[:, None]
+        exact[(N, ld)] = (inst, tt, s.utilisation(), float((served * tt).sum() / served.sum()))
+        s.close()
+    rows = {}
+    gpu_s, calls = 0.0, 0
+    for kind in kinds:
+        mrt_err, util_err = [], []
+        for N, ld in cases:
+            inst, tt, rho, mrt = exact[(N, ld)]
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            g = hq.hq_des_simulate(N, inst.J, inst.lam_j, inst.nu, inst.pref, tt, kind, reps, arr, warm, 17)
+            gpu_s += time.perf_counter() - t0
+            calls += reps * arr
+            e = oracle.des_summary(g["busy"], g["served"], g["lost"], g["window"], g["resp"], arr - warm)
+            mrt_err.append(100 * abs(e["mrt"] - mrt) / e["mrt"])
+            util_err.append(100 * float(np.mean(np.abs(e["util"] - rho) / e["util"])))
+        rows[kind] = {"mpre_mrt_pct": round(float(np.mean(mrt_err)), 4),
+                      "mpre_mrt_max_pct": round(float(np.max(mrt_err)), 4),
+                      "mpre_util_pct": round(float(np.mean(util_err)), 4),
+                      "mpre_util_max_pct": round(float(np.max(util_err)), 4)}
+    # the oracle's simulation of one case on one host core, bounded sample
+    inst, tt, _, _ = exact[(10, 0.5)]
+    t0 = time.perf_counter()
+    oracle.des_loss(inst, travel=tt, kind="lognormal", reps=8, arrivals=200_000, warmup=400, seed=17)
+    cpu_s = time.perf_counter() - t0
+    line = {"metric": "Section 5.5 check: MPRE of MRT and utilisation, GPU simulation vs hypercube "
+                      "solution (15 cases per service distribution)",
+            "value": calls / gpu_s, "unit": "simulated calls/s", "n_gpus": 1, "higher_is_better": True,
+            "data": "synthetic", "dtype": "f64",
+            "config": {"workload": "des_n8_12_j71_loads0.1-0.9", "replications": reps, "calls": arr,
+                       "warmup_calls": warm, "cases": len(cases)},
+            "mpre": rows, "gpu_seconds": gpu_s,
+            "cpu_baseline": {"value": 8 * 200_000 / cpu_s, "unit": "simulated calls/s", "cores": 1,
+                             "kind": "oracle", "sample": "8 replications of 200,000 calls, N=10, load 0.5, "
+                                                          "log-normal service"}}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse()
+    if args.des:
+        return run_des(args)
     if args.fp_rate:
         return run_fp_rate(args)
     if args.warmstart:

@@ -359,6 +359,34 @@ int hq_mlp_predict(hq_solver* h, hq_mlp* m, double* q, double* pn, double* rho, 
 int hq_attach_mlp(hq_solver* h, hq_mlp* m);
 void hq_mlp_destroy(hq_mlp* m);
 
+/* ---- discrete-event simulation of the loss system (Section 5.5) -----------------------
+ * The paper checks its exponential-service solution against simulations of the loss
+ * system with other service-time distributions of the same means (Section 5.5, its
+ * Table of MRT and utilisation errors): for a system without a queue the stationary
+ * solution is insensitive to the service distribution.  hq_des_simulate runs `reps`
+ * independent replications of that system on the GPU, one thread each: Poisson
+ * arrivals of rate sum_j lambda_j, node j with probability lambda_j / lambda, the first
+ * idle unit of pref row j serves (Section 2.1), else the call is lost; unit i's service
+ * times have mean 1/nu_i and shape service_kind: 0 exponential, 1 log-normal with the
+ * exponential's variance, 2 gamma of shape 5 (scale 1/(5 nu_i)), 3 gamma of shape 1/2
+ * (scale 2/nu_i), 4 uniform on [0, 2/nu_i].  Each replication starts empty; arrivals
+ * 0..warmup-1 are not counted; the window runs from arrival `warmup` to the last of
+ * `arrivals`.  Random numbers: a counter-based splitmix64 stream per replication (key
+ * from `seed` and the replication index), 8 draws per arrival.
+ *   N 1..32, J >= 1; lambda_j (J), nu (N), pref (J*N int32 rows, permutations of
+ *   0..N-1), travel (J*N doubles, travel[j*N + i] = response time of unit i to node j):
+ *   inputs.  Outputs: busy (reps*N: busy time of unit i in the window, exact overlap),
+ *   served (reps*N int64: calls served in the window), lost (reps int64), window (reps:
+ *   window length), resp (reps: summed travel time of the calls served in the window).
+ *   mem: HQ_HOST or HQ_DEVICE for every array; stream as for hq_create.  Utilisation is
+ *   busy / window, the mean response time resp / sum(served).  Blocks until done.
+ *   Errors: HQ_EINVAL (sizes, kind, NULL, a bad pref row, negative or non-finite rates),
+ *   HQ_ECUDA. */
+int hq_des_simulate(int N, int J, const double* lambda_j, const double* nu, const int32_t* pref,
+                    const double* travel, int service_kind, int64_t reps, int64_t arrivals,
+                    int64_t warmup, uint64_t seed, double* busy, int64_t* served, int64_t* lost,
+                    double* window, double* resp, int mem, void* stream);
+
 /* Release a solver and every device buffer it holds (the model of hq_create; not in
  * the paper).  NULL is ignored.  A model attached by hq_attach_mlp is not freed. */
 void hq_destroy(hq_solver* h);

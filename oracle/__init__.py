@@ -28,6 +28,7 @@ LOSS, FINITE, INFINITE = 0, 1, 2
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "hq_oracle.c")
+_SRCS = [_SRC, os.path.join(_HERE, "des.c")]
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 _LIB_OMP_PATH = os.path.join(_BUILD, "liboracle_omp.so")
@@ -46,11 +47,11 @@ _vp = ctypes.c_void_p
 
 def _compile(path: str, omp: bool, force: bool) -> str:
     os.makedirs(_BUILD, exist_ok=True)
-    stale = not os.path.exists(path) or os.path.getmtime(path) < os.path.getmtime(_SRC)
+    stale = not os.path.exists(path) or any(os.path.getmtime(path) < os.path.getmtime(s) for s in _SRCS)
     if force or stale:
         tmp = path + f".tmp{os.getpid()}"
         cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fno-fast-math",
-               "-ffp-contract=off", *(["-fopenmp"] if omp else []), _SRC, "-o", tmp, "-lm"]
+               "-ffp-contract=off", *(["-fopenmp"] if omp else []), *_SRCS, "-o", tmp, "-lm"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, path)
     return path
@@ -113,6 +114,11 @@ def _load(threads: int = 1):
             "or_sampled_balance": (None, [_i, _i, _pd, _pd, _pi32, _i, _i64, _pu64, _pd, _pd, _d,
                                           _pd, _pd]),
             "or_threads": (_i, [_i]),
+            "or_des_loss": (_i, [_i, _i, _pd, _pd, _pi32, _pd, _i, _i64, _i64, _i64, ctypes.c_uint64,
+                                 _pd, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                                 _pd, _pd]),
+            "or_des_service": (_d, [_i, _d, ctypes.c_uint64, ctypes.c_uint64]),
+            "or_des_uniform": (_d, [ctypes.c_uint64, _i64, ctypes.c_uint64]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -370,3 +376,45 @@ def sampled_balance(inst, B, Pself, Pnb, pq1=0.0):
                            _p(B, _pu64), _p(Pself, _pd), _p(Pnb, _pd), float(pq1), _p(out, _pd),
                            _p(inn, _pd))
     return out, inn
+
+
+# ---- discrete-event simulation of the loss system (des.c) -----------------------------
+
+DES_KINDS = {"exponential": 0, "lognormal": 1, "gamma5": 2, "gamma05": 3, "uniform": 4}
+
+
+def des_loss(inst=None, travel=None, kind: str | int = "exponential", reps: int = 20,
+             arrivals: int = 100_000, warmup: int = 1000, seed: int = 1, **kw) -> dict:
+    """Simulate the loss system (Section 5.5): per replication and unit the busy time in
+    the window and the calls served, per replication the calls lost, the window length
+    and the summed travel time of served calls; plus the estimates built from them
+    (utilisation, loss probability, mean response time), averaged over replications."""
+    lib = _load(1)
+    N, J, lam_j, nu, pref, mode, C = _args(inst, **kw)
+    travel = np.ascontiguousarray(travel if travel is not None else np.zeros((J, N)), dtype=np.float64)
+    k = DES_KINDS[kind] if isinstance(kind, str) else int(kind)
+    busy = np.empty((reps, N))
+    served = np.empty((reps, N), dtype=np.int64)
+    lost = np.empty(reps, dtype=np.int64)
+    window = np.empty(reps)
+    resp = np.empty(reps)
+    _pi64 = ctypes.POINTER(ctypes.c_int64)
+    rc = lib.or_des_loss(N, J, _p(lam_j, _pd), _p(nu, _pd), _p(pref, _pi32), _p(travel, _pd), k, reps,
+                         arrivals, warmup, ctypes.c_uint64(seed), _p(busy, _pd), _p(served, _pi64),
+                         _p(lost, _pi64), _p(window, _pd), _p(resp, _pd))
+    if rc != 0:
+        raise ValueError("oracle DES rejected its arguments")
+    return des_summary(busy, served, lost, window, resp, arrivals - warmup)
+
+
+def des_summary(busy, served, lost, window, resp, counted) -> dict:
+    """Estimates from the per-replication totals: utilisation busy/window (mean and
+    standard error over replications), loss probability, mean response time."""
+    util = busy / window[:, None]
+    reps = busy.shape[0]
+    se = util.std(axis=0, ddof=1) / np.sqrt(reps) if reps > 1 else np.full(busy.shape[1], np.nan)
+    nserved = served.sum(axis=1)
+    mrt = resp / np.maximum(nserved, 1)
+    return dict(busy=busy, served=served, lost=lost, window=window, resp=resp,
+                util=util.mean(axis=0), util_se=se, p_lost=float(lost.sum() / (reps * counted)),
+                mrt=float(mrt.mean()), mrt_se=float(mrt.std(ddof=1) / np.sqrt(reps)) if reps > 1 else float("nan"))

@@ -101,6 +101,8 @@ _SIGS = {
     "hq_mlp_predict": (_i, [_vp, _vp, _vp, _vp, _vp, _i]),
     "hq_attach_mlp": (_i, [_vp, _vp]),
     "hq_mlp_destroy": (None, [_vp]),
+    "hq_des_simulate": (_i, [_i, _i, _vp, _vp, _vp, _vp, _i, ctypes.c_int64, ctypes.c_int64,
+                             ctypes.c_int64, ctypes.c_uint64, _vp, _vp, _vp, _vp, _vp, _i, _vp]),
 }
 
 
@@ -504,3 +506,45 @@ class Solver:
 
     def __exit__(self, *a):
         self.close()
+
+
+# ---- discrete-event simulation of the loss system -------------------------------------
+
+DES_KINDS = {"exponential": 0, "lognormal": 1, "gamma5": 2, "gamma05": 3, "uniform": 4}
+
+
+def hq_des_simulate(N: int, J: int, lam_j, nu, pref, travel, kind, reps: int, arrivals: int,
+                    warmup: int, seed: int, stream=None) -> dict:
+    """Run hq_des_simulate on host arrays (numpy) or device tensors (torch, all on the
+    same device); returns the per-replication outputs as arrays of the same kind."""
+    k = DES_KINDS[kind] if isinstance(kind, str) else int(kind)
+    if isinstance(lam_j, np.ndarray) or not hasattr(lam_j, "is_cuda"):
+        lam_j = np.ascontiguousarray(lam_j, dtype=np.float64)
+        nu = np.ascontiguousarray(nu, dtype=np.float64)
+        pref = np.ascontiguousarray(pref, dtype=np.int32)
+        travel = np.ascontiguousarray(travel, dtype=np.float64)
+        for a, n in ((lam_j, J), (nu, N), (pref, J * N), (travel, J * N)):
+            if a.size != n:
+                raise ValueError("hq_des_simulate: input of the wrong size")
+        out = dict(busy=np.empty((reps, N)), served=np.empty((reps, N), dtype=np.int64),
+                   lost=np.empty(reps, dtype=np.int64), window=np.empty(reps), resp=np.empty(reps))
+        mem = HQ_HOST
+    else:
+        import torch
+
+        dev = lam_j.device
+        out = dict(busy=torch.empty((reps, N), dtype=torch.float64, device=dev),
+                   served=torch.empty((reps, N), dtype=torch.int64, device=dev),
+                   lost=torch.empty(reps, dtype=torch.int64, device=dev),
+                   window=torch.empty(reps, dtype=torch.float64, device=dev),
+                   resp=torch.empty(reps, dtype=torch.float64, device=dev))
+        for a, dt in ((lam_j, torch.float64), (nu, torch.float64), (pref, torch.int32), (travel, torch.float64)):
+            if a.dtype != dt or not a.is_cuda or not a.is_contiguous():
+                raise ValueError("hq_des_simulate: device inputs must be contiguous CUDA tensors "
+                                 "(float64 rates and travel times, int32 preferences)")
+        mem = HQ_DEVICE
+    pa = [_ptr(x)[0] for x in (lam_j, nu, pref, travel)]
+    po = [_ptr(out[k2])[0] for k2 in ("busy", "served", "lost", "window", "resp")]
+    sp = stream.cuda_stream if stream is not None and hasattr(stream, "cuda_stream") else stream
+    _check(load().hq_des_simulate(N, J, *pa, k, reps, arrivals, warmup, ctypes.c_uint64(seed), *po, mem, sp))
+    return out

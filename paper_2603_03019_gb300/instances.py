@@ -196,3 +196,20 @@ def homogeneous_instance(N: int, J: int, seed: int, load: float, nu: float = 1.0
     inst.nu = np.full(N, float(nu))
     inst.lam_j = inst.lam_j / inst.lam_j.sum() * load * N * nu
     return inst
+
+
+# ---- inputs of the discrete-event simulation (Section 5.5) ------------------------------
+
+def travel_times(inst: Instance) -> np.ndarray:
+    """J x N response times: the Euclidean distance from unit i's station to node j in the
+    unit square (a synthetic stand-in for the paper's road travel times)."""
+    d = inst.nodes_xy[:, None, :] - inst.units_xy[None, :, :]
+    return np.sqrt((d * d).sum(axis=2))
+
+
+def des_instance(seed: int, N: int = 10, load: float = 0.5, J: int = 71) -> Instance:
+    """Loss-system instances of the service-distribution check: N = 8..12 units, J = 71
+    demand nodes uniform in the unit square (the St. Paul case has 71 census tracts),
+    nu_i = 1 +- U[-0.2, 0.2] (the paper's heterogeneity adjustment), a given load."""
+    return geometric_instance(N, J, seed, load, nu_lo=0.8, nu_hi=1.2,
+                              name=f"des_n{N}_j{J}_l{load}_s{seed}")
