@@ -723,9 +723,11 @@ def run_des(args):
     {0.1, 0.3, 0.5, 0.7, 0.9} (15 cases) and each service distribution, the GPU
     simulation's mean response time and unit utilisations against the exact loss-system
     solution (GPU, FP64, 1e-12 residual): MPRE in per cent as in the paper's Eq. for
-    MPRE.  Per case 1,280 replications of 16,000 calls (400 not counted): the same 2e7
-    calls as the paper's 20 replications of 10^6.  Beside it the oracle's simulation on
-    one host core, timed on a bounded sample."""
+    MPRE.  Per case 38,912 replications (256 per SM) of 1,000 calls, the first 200 not
+    counted: 3.1e7 counted calls, more than the paper's 20 replications of 10^6, spread
+    over enough independent replications to fill the GPU (each replication is one
+    thread's sequential event loop).  Beside it the oracle's simulation on one host
+    core, timed on a bounded sample."""
     import torch
 
     import oracle
@@ -733,7 +735,7 @@ def run_des(args):
 
     hq.load()
     kinds = ["exponential", "lognormal", "gamma5", "gamma05", "uniform"]
-    reps, arr, warm = 1280, 16_000, 400
+    reps, arr, warm = 38_912, 1_000, 200
     cases = [(N, ld) for N in (8, 10, 12) for ld in (0.1, 0.3, 0.5, 0.7, 0.9)]
     exact = {}
     for N, ld in cases:

@@ -408,13 +408,20 @@ def des_loss(inst=None, travel=None, kind: str | int = "exponential", reps: int 
 
 
 def des_summary(busy, served, lost, window, resp, counted) -> dict:
-    """Estimates from the per-replication totals: utilisation busy/window (mean and
-    standard error over replications), loss probability, mean response time."""
-    util = busy / window[:, None]
+    """Estimates from the per-replication totals, pooled over replications (ratios of
+    sums, which carry no 1/window bias): utilisation = total busy time / total window,
+    loss probability, mean response time = total travel time / calls served; standard
+    errors from the spread of the per-replication ratios."""
+    busy, window, resp = np.asarray(busy), np.asarray(window), np.asarray(resp)
+    served, lost = np.asarray(served), np.asarray(lost)
     reps = busy.shape[0]
-    se = util.std(axis=0, ddof=1) / np.sqrt(reps) if reps > 1 else np.full(busy.shape[1], np.nan)
     nserved = served.sum(axis=1)
-    mrt = resp / np.maximum(nserved, 1)
-    return dict(busy=busy, served=served, lost=lost, window=window, resp=resp,
-                util=util.mean(axis=0), util_se=se, p_lost=float(lost.sum() / (reps * counted)),
-                mrt=float(mrt.mean()), mrt_se=float(mrt.std(ddof=1) / np.sqrt(reps)) if reps > 1 else float("nan"))
+    util = busy.sum(axis=0) / window.sum()
+    mrt = float(resp.sum() / max(int(nserved.sum()), 1))
+    if reps > 1:
+        se = (busy / window[:, None]).std(axis=0, ddof=1) / np.sqrt(reps)
+        mrt_se = float((resp / np.maximum(nserved, 1)).std(ddof=1) / np.sqrt(reps))
+    else:
+        se, mrt_se = np.full(busy.shape[1], np.nan), float("nan")
+    return dict(busy=busy, served=served, lost=lost, window=window, resp=resp, util=util, util_se=se,
+                p_lost=float(lost.sum() / (reps * counted)), mrt=mrt, mrt_se=mrt_se)
