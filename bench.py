@@ -39,6 +39,7 @@ sys.path.insert(0, ROOT)
 from paper_2603_03019_gb300 import instances as I  # noqa: E402
 
 WORKLOADS = {
+    "n29": lambda seed: I.large_infinite_n24(seed, N=29),
     "n28": lambda seed: I.large_infinite_n24(seed, N=28),
     "n26": lambda seed: I.large_infinite_n24(seed, N=26),
     "n24": lambda seed: I.large_infinite_n24(seed),
@@ -62,7 +63,7 @@ METRIC = "N=24 time-to-1e-10 residual: warm-start+FP32 vs plain FP64; state-upda
 # the plain FP64 sweep's ALU ceiling (fraction of HBM peak), from the measured FP64
 # FMA rate and the sweep's FP64 operations per algorithmic byte; None until measured
 FP64_ALU_CEILING = None
-BASE_SEED = {"n28": 3001, "n26": 3001, "n24": 3001, "n23": 3001, "n22": 3001, "n20": 2001, "n10": 1001}
+BASE_SEED = {"n29": 3001, "n28": 3001, "n26": 3001, "n24": 3001, "n23": 3001, "n22": 3001, "n20": 2001, "n10": 1001}
 
 
 def parse():
@@ -461,6 +462,8 @@ def run_ours(args):
                     ("fp64+sor", "fp64", -1.0, RB, W0),
                     ("fp64 redblack", "fp64", 1.0, RB, W0))
             for name, pname, om, so, warm in runs:
+                if "df64" in pname and N > 28:
+                    continue  # double-float tables are not kept above N = 28
                 rows = []
                 for _ in range(max(1, args.repeats)):
                     rc, st = hq.hq_solve(solver.h, opts(hq.PRECISION[pname], omega=om, sweep_order=so,
@@ -491,6 +494,8 @@ def run_ours(args):
                 hq.hq_solve(solver.h, opts(tol=1.0, sweep_order=so))
                 for name, pc in (("fp32", hq.HQ_PREC_FP32), ("ir", hq.HQ_PREC_FP32_IR),
                                  ("df64", hq.HQ_PREC_DF64), ("fp64", hq.HQ_PREC_FP64)):
+                    if name == "df64" and N > 28:
+                        continue
                     msw = statistics.median(hq.hq_profile_sweep(solver.h, pc, 8) for _ in range(3))
                     nbytes = hq.hq_sweep_bytes(solver.h, pc)
                     ach = nbytes / (msw / 1000.0) / 1e9

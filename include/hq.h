@@ -145,13 +145,17 @@ void hq_default_opts(hq_opts* opts);
 /* The model of Section 2.1 (N units with their own service rates, J demand nodes with
  * preference lists, first-idle dispatch) in the loss form, the finite-buffer form of
  * Section 2.2's finite-buffer reformulation or the infinite-queue form of its Remark.
- * Allocate a solver for N units (1..28), J nodes (>= 1) and a queue mode
+ * Allocate a solver for N units (1..29), J nodes (>= 1) and a queue mode
  * (capacity_C >= 1 iff HQ_FINITE, ignored otherwise) on the current device.
  * stream: a cudaStream_t, or NULL for the default stream.  Allocates every device
- * buffer the solve needs: about 14 N 2^N bytes for the upward-rate table in FP64,
- * double-float and FP32 and the transform scratch, plus about 104 bytes per state
- * (masks, neighbour positions, iterates and r in three precisions, the refinement's
- * base and base terms, the outputs); e.g. 7.4 GB at N=24, 130 GB at N=28.  Builds
+ * buffer the solve needs: the upward-rate table in FP64, double-float and FP32 (state
+ * records padded to a multiple of 4 rates: about 20 (N/2 + 1.5) 2^N bytes) and the
+ * transform scratch (4 N 2^N bytes), plus about 124 bytes per state (masks, iterates and
+ * r in three precisions, weights, the refinement's base and base terms, the outputs);
+ * e.g. 8.2 GB at N=24, 146 GB at N=28.  At N = 29 the double-float table and iterates
+ * and the batched kernel's lists are not allocated (the rest is about 215 GB):
+ * HQ_PREC_DF64 and HQ_PREC_FP32_DF64 return HQ_EINVAL there, and hq_batch_create takes
+ * N <= 28.  Builds
  * the N-dependent layout (layer-ranked state masks and rank tables).  Writes the
  * handle to *out. */
 int hq_create(int N, int J, int mode, int capacity_C, void* stream, hq_solver** out);

@@ -101,7 +101,7 @@ static int dalloc(hq_solver* h, T** p, int64_t bytes) {
 extern "C" int hq_create(int N, int J, int mode, int capacity_C, void* stream, hq_solver** out) {
   if (!out) { hq_set_error("out is NULL"); return HQ_EINVAL; }
   *out = nullptr;
-  if (N < 1 || N > HQ_MAXN) { hq_set_error("N must be in 1..28"); return HQ_EINVAL; }
+  if (N < 1 || N > HQ_MAXN) { hq_set_error("N must be in 1..29"); return HQ_EINVAL; }
   if (J < 1) { hq_set_error("J must be >= 1"); return HQ_EINVAL; }
   if (mode < HQ_LOSS || mode > HQ_INFINITE) { hq_set_error("mode must be 0, 1 or 2"); return HQ_EINVAL; }
   if (mode == HQ_FINITE && (capacity_C < 1 || capacity_C > (1 << 20))) {
@@ -157,17 +157,18 @@ extern "C" int hq_create(int N, int J, int mode, int capacity_C, void* stream, h
   HQ_TRY(dalloc(h, &h->pre, (int64_t)J * N * 4));
   HQ_TRY(dalloc(h, &h->zeta, half * N * 8));
   HQ_TRY(dalloc(h, (double**)&h->b64.T, TE * 8));
-  HQ_TRY(dalloc(h, (float2**)&h->bdf.T, TE * 8));
+  const bool df = N <= HQ_DF_MAXN;  // double-float table, iterates and batch lists
+  if (df) HQ_TRY(dalloc(h, (float2**)&h->bdf.T, TE * 8));
   HQ_TRY(dalloc(h, (float**)&h->b32.T, TE * 4));
-  HQ_TRY(dalloc(h, &h->lidx, SP * 12));
+  if (df) HQ_TRY(dalloc(h, &h->lidx, SP * 12));
   HQ_TRY(dalloc(h, &h->wfeat, (int64_t)HQ_MAXN * HQ_MAXN * HQ_MLP_FEATURES * 4));
   HQ_TRY(dalloc(h, &h->wy, (int64_t)HQ_MAXN * HQ_MAXN * 4));
   HQ_TRY(dalloc(h, &h->wlx, ((int64_t)HQ_MAXN * HQ_MAXN + HQ_MAXN + 1) * 8));
   HQ_TRY(dalloc(h, (double**)&h->b64.r, SP * 8));
-  HQ_TRY(dalloc(h, (float2**)&h->bdf.r, SP * 8));
+  if (df) HQ_TRY(dalloc(h, (float2**)&h->bdf.r, SP * 8));
   HQ_TRY(dalloc(h, (float**)&h->b32.r, SP * 4));
   HQ_TRY(dalloc(h, (double**)&h->b64.p, SP * 8));
-  HQ_TRY(dalloc(h, (float2**)&h->bdf.p, SP * 8));
+  if (df) HQ_TRY(dalloc(h, (float2**)&h->bdf.p, SP * 8));
   HQ_TRY(dalloc(h, (float**)&h->b32.p, SP * 4));
   HQ_TRY(dalloc(h, &h->ir_base, SP * 8));
   HQ_TRY(dalloc(h, &h->ir, SP * 12));
@@ -209,7 +210,7 @@ extern "C" int hq_create(int N, int J, int mode, int capacity_C, void* stream, h
     int64_t zero_len[] = {SP * 4, TE * 8, SP * 8, SP * 8, SP * 4, SP * 8, SP * 8, SP * 4,
                           2 * h->ab_half_bytes, SP * 8, SP * 12, SP * 16, SP * 8};
     for (int i = 0; i < 13 && e == cudaSuccess; i++)
-      e = cudaMemsetAsync(zero_bufs[i], 0, (size_t)zero_len[i], h->stream);
+      if (zero_bufs[i]) e = cudaMemsetAsync(zero_bufs[i], 0, (size_t)zero_len[i], h->stream);
   }
   if (e != cudaSuccess) {
     int rc = hq_cuda_fail(e, "cudaMemsetAsync", __FILE__, __LINE__);
@@ -302,6 +303,10 @@ extern "C" int hq_solve(hq_solver* h, const hq_opts* opts_in, hq_stats* stats) {
     return HQ_EINVAL;
   }
   if (o.debug_barrier < 0) { hq_set_error("debug_barrier must be >= 0"); return HQ_EINVAL; }
+  if (!h->bdf.T && (o.precision == HQ_PREC_DF64 || o.precision == HQ_PREC_FP32_DF64)) {
+    hq_set_error("double-float precisions are not kept above N = 28 (memory)");
+    return HQ_EINVAL;
+  }
   h->order = o.sweep_order;
   // fault injection (tests): CTA debug_barrier - 1 skips its first grid-barrier arrival in
   // the first sweep launch, and every bounded wait gives up after 2^20 polls
@@ -696,6 +701,10 @@ extern "C" int hq_profile_sweep(hq_solver* h, int precision, int sweeps, float* 
   }
   ms_out[0] = 0.f;
   if (h->N < 2) return HQ_OK;
+  if (precision == HQ_PREC_DF64 && !h->bdf.T) {
+    hq_set_error("double-float precisions are not kept above N = 28 (memory)");
+    return HQ_EINVAL;
+  }
   if (precision == HQ_PREC_FP32_IR) precision = HQ_PREC_IRC;  // correction sweeps
   if (h->cur_prec != precision) {
     rc = hq_convert_iterate(h, h->cur_prec, precision);

@@ -465,6 +465,7 @@ extern "C" int hq_batch_create(hq_solver* const* solvers, int count, void* strea
     if (!solvers[c]) { hq_set_error("NULL solver in the batch"); return HQ_EINVAL; }
     if (!solvers[c]->loaded) { hq_set_error("every solver of a batch must be loaded"); return HQ_ESTATE; }
     if (solvers[c]->N < 2) { hq_set_error("batched solvers need N >= 2"); return HQ_EINVAL; }
+    if (solvers[c]->N > HQ_DF_MAXN) { hq_set_error("batched solvers need N <= 28"); return HQ_EINVAL; }
   }
   hq_batch* b = new hq_batch();
   b->K = count;

@@ -10,7 +10,12 @@
 
 #include "../../include/hq.h"
 
-#define HQ_MAXN 28
+#define HQ_MAXN 29
+// Largest N for which the solver keeps the double-float table and iterates and the
+// batched kernel's per-state lists (at N = 29 they would not fit beside the FP64 and FP32
+// tables in the GPU's memory): above it the double-float precisions and batching are
+// unavailable.
+#define HQ_DF_MAXN 28
 #define HQ_LO_BITS 10          // low-part width of the split rank tables
 #define HQ_THREADS 256         // threads per CTA of the streaming kernels
 
@@ -25,10 +30,11 @@
 // rank of block (hi, w-1) in layer n-1, rank of block (hi, w+1) in layer n+1}.
 #define HQ_ITEM_HI_BITS 20
 // Items of the direct sweep (hq_persist.cu): runs of at most HQ_SW_ITEM consecutive states
-// of one rank block, 8 bytes: x = hi | w << 18 | (count-1) << 22, y = rank of the item's
-// first state in layer n | n << 27.  The sweep takes its high-part neighbour bases, its
-// own block base and its low-part neighbour blocks from RH once per rank block.
-#define HQ_SW_HI_BITS 18
+// of one rank block, 8 bytes: x = hi | w << 20 | (count-1) << 24, y = rank of the item's
+// first state in layer n | n << 27 (ranks below 2^27: C(29, 14) = 7.8e7).  The sweep takes
+// its high-part neighbour bases, its own block base and its low-part neighbour blocks
+// from RH once per rank block.
+#define HQ_SW_HI_BITS 20
 #define HQ_SW_ITEM 32
 #define HQ_MLP_UNIT_FEATURES 8  // per-unit features of an instance
 #define HQ_MLP_FEATURES 9       // inputs of the warm-start network: unit features + n / N

@@ -59,7 +59,7 @@ __global__ void k_table_conv(int64_t n, const double* T64, float* T32, float2* T
   if (i >= n) return;
   const double v = T64[i];
   T32[i] = (float)v;
-  Tdf[i] = df_from_double(v);
+  if (Tdf) Tdf[i] = df_from_double(v);
 }
 
 }  // namespace
@@ -129,7 +129,7 @@ int hq_sweep_item_list(int N, int order, std::vector<uint2>& items, std::vector<
       blocks.push_back((int)items.size());
       for (int s0 = 0; s0 < size; s0 += HQ_SW_ITEM) {
         const int c = size - s0 < HQ_SW_ITEM ? size - s0 : HQ_SW_ITEM;
-        items.push_back(make_uint2(hi | ((uint32_t)w << HQ_SW_HI_BITS) | ((uint32_t)(c - 1) << 22),
+        items.push_back(make_uint2(hi | ((uint32_t)w << HQ_SW_HI_BITS) | ((uint32_t)(c - 1) << (HQ_SW_HI_BITS + 4)),
                                    (uint32_t)(start + (uint64_t)s0) | ((uint32_t)n << 27)));
       }
     }
@@ -197,6 +197,7 @@ int hq_build_items(hq_solver* h) {
       HQ_CUDA(cudaMemcpyAsync(h->sperm[order], perm.data(), pbytes, cudaMemcpyHostToDevice, h->stream));
     HQ_CUDA(cudaStreamSynchronize(h->stream));  // the host vectors go out of scope
   }
+  if (h->N > HQ_DF_MAXN) return HQ_OK;  // the batched kernel's lists: not kept above HQ_DF_MAXN
   std::vector<uint4> items;
   const int rc = hq_item_list(h->N, items, h->ifirst);
   if (rc != HQ_OK) return rc;

@@ -194,7 +194,7 @@ __global__ void k_rates(LayoutArgs la, int64_t S, const uint32_t* masks, const d
   double lm = (n == N) ? lam_full : lam;
   double r = 1.0 / (lm + mu);
   r64[g] = r;
-  rdf[g] = df_from_double(r);
+  if (rdf) rdf[g] = df_from_double(r);
   r32[g] = (float)r;
 }
 

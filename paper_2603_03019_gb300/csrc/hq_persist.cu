@@ -443,7 +443,7 @@ __device__ __forceinline__ void run_items(Smem<V, kWarps, kHP>& s, const SweepAr
   auto issue = [&](int it, int bq, ItemRef& ir, ItemLoads<V, kNV, kHP>& ld) {
     const BlockCtx<V> c = bq ? bc1 : bc0;
     const uint2 d = __ldg(a.items + it);
-    ir.cnt = (int)((d.x >> 22) & 0x3fu) + 1;
+    ir.cnt = (int)((d.x >> (HQ_SW_HI_BITS + 4)) & 0x1fu) + 1;
     ir.bq = bq;
     const bool act = lane < ir.cnt;
     ir.rk = (d.y & ((1u << 27) - 1u)) + (act ? (uint32_t)lane : 0u);
@@ -942,11 +942,14 @@ constexpr int kSweepThreadsWide = 384;
 // 1.36 vs 1.63 and 1.80 ms per red-black sweep, FP64 1.98 vs 2.00 and 2.21 ms.
 int sweep_threads(int, int kind) { return kind == HQ_PREC_FP32 ? kSweepThreads : kSweepThreadsWide; }
 
+// high-part list sizes: 14 (N <= 24), 18 (N <= 28), 20 (N = 29; no double-float there)
 template <class V, bool kIR>
 const void* sweep_fn(int H) {
   constexpr int kT = V::kind == HQ_PREC_FP32 ? kSweepThreads : kSweepThreadsWide;
   if (H <= 14) return (const void*)k_sweep<V, kIR, 14, kT>;
-  return (const void*)k_sweep<V, kIR, 18, kT>;
+  if (H <= 18) return (const void*)k_sweep<V, kIR, 18, kT>;
+  if constexpr (V::kind != HQ_PREC_DF64) return (const void*)k_sweep<V, kIR, 20, kT>;
+  return nullptr;
 }
 
 int g_nsm = 0;
@@ -1012,6 +1015,10 @@ int sweep_grid(hq_solver* h, bool ir, int* G) {
   const int thr = sweep_threads(h->H, V::kind);
   const size_t smem = (size_t)(thr / 32) * kSlotBytes<V>();
   const void* kfn = ir ? sweep_fn<PolF32, true>(h->H) : sweep_fn<V, false>(h->H);
+  if (!kfn) {
+    hq_set_error("no sweep kernel for this precision at this N");
+    return HQ_EINVAL;
+  }
   if (!g_nsm) HQ_CUDA(cudaDeviceGetAttribute(&g_nsm, cudaDevAttrMultiProcessorCount, h->dev));
   HQ_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int occ = 0;
@@ -1072,13 +1079,14 @@ int hq_base_pass(hq_solver* h) {
   a.nu = h->b64.nu;
   a.wv = h->wv64;
   a.out = h->ir;
-  const size_t smem = (size_t)(kSweepThreads / 32) * kSlotBytes<PolF64>();
-  const void* kfn = h->H <= 14 ? (const void*)k_base_pass<14, kSweepThreads>
-                               : (const void*)k_base_pass<18, kSweepThreads>;
+  const size_t smem = (size_t)(kSweepThreadsWide / 32) * kSlotBytes<PolF64>();
+  const void* kfn = h->H <= 14   ? (const void*)k_base_pass<14, kSweepThreadsWide>
+                    : h->H <= 18 ? (const void*)k_base_pass<18, kSweepThreadsWide>
+                                 : (const void*)k_base_pass<20, kSweepThreadsWide>;
   HQ_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   if (!g_nsm) HQ_CUDA(cudaDeviceGetAttribute(&g_nsm, cudaDevAttrMultiProcessorCount, h->dev));
   void* args[] = {&a};
-  HQ_CUDA(cudaLaunchKernel(kfn, dim3(g_nsm), dim3(kSweepThreads), args, smem, h->stream));
+  HQ_CUDA(cudaLaunchKernel(kfn, dim3(g_nsm), dim3(kSweepThreadsWide), args, smem, h->stream));
   HQ_LAUNCHED();
   return HQ_OK;
 }
@@ -1095,12 +1103,13 @@ int hq_residual_fused(hq_solver* h) {
   a.wv = h->wv64;
   HQ_CUDA(cudaMemsetAsync(&h->sc->res_num[0], 0, sizeof(double) * (HQ_MAXN + 1), h->stream));
   HQ_CUDA(cudaMemsetAsync(&h->sc->res_den[0], 0, sizeof(double) * (HQ_MAXN + 1), h->stream));
-  const size_t smem = (size_t)(kSweepThreads / 32) * kSlotBytes<PolF64>();
-  const void* kfn = h->H <= 14 ? (const void*)k_residual_fused<14, kSweepThreads>
-                               : (const void*)k_residual_fused<18, kSweepThreads>;
+  const size_t smem = (size_t)(kSweepThreadsWide / 32) * kSlotBytes<PolF64>();
+  const void* kfn = h->H <= 14   ? (const void*)k_residual_fused<14, kSweepThreadsWide>
+                    : h->H <= 18 ? (const void*)k_residual_fused<18, kSweepThreadsWide>
+                                 : (const void*)k_residual_fused<20, kSweepThreadsWide>;
   HQ_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   void* args[] = {&a};
-  HQ_CUDA(cudaLaunchKernel(kfn, dim3(g_nsm), dim3(kSweepThreads), args, smem, h->stream));
+  HQ_CUDA(cudaLaunchKernel(kfn, dim3(g_nsm), dim3(kSweepThreadsWide), args, smem, h->stream));
   HQ_LAUNCHED();
   return HQ_OK;
 }

@@ -51,7 +51,7 @@ def test_library_is_built_for_sm103a():
 def test_invalid_arguments_rejected_without_gpu(lib):
     h = ctypes.c_void_p()
     assert lib.hq_create(0, 5, 0, 0, None, ctypes.byref(h)) == hq.HQ_EINVAL
-    assert lib.hq_create(29, 5, 0, 0, None, ctypes.byref(h)) == hq.HQ_EINVAL
+    assert lib.hq_create(30, 5, 0, 0, None, ctypes.byref(h)) == hq.HQ_EINVAL
     assert lib.hq_create(8, 0, 0, 0, None, ctypes.byref(h)) == hq.HQ_EINVAL
     assert lib.hq_create(8, 5, 7, 0, None, ctypes.byref(h)) == hq.HQ_EINVAL
     assert lib.hq_create(8, 5, hq.HQ_FINITE, 0, None, ctypes.byref(h)) == hq.HQ_EINVAL

@@ -178,3 +178,53 @@ def test_n26_sampled(gpu_lib):
     assert np.allclose(R.sum(axis=1), 1.0, rtol=0, atol=1e-10)
     bound = (1 << (N - 1)) * summ["residual"] * den
     assert np.max(np.abs(inst.lam_j @ R - inst.nu * rho)) <= bound
+
+
+def test_n29_sampled_balance(gpu_lib):
+    """N=29 (2^29 = 537M states, the largest size the solver allocates: 215.5 GB of
+    device memory without the double-float precisions), J=1000, the benchmark's options:
+    sampled global balance of Eq. (1) with the oracle's dispatch rule (which checks the
+    table through the solution), normalisation and flow balance.  Needs a GPU with
+    about 230 GB free."""
+    import torch
+
+    free, _ = torch.cuda.mem_get_info()
+    if free < 230e9:
+        pytest.skip(f"N=29 needs about 230 GB of free device memory, {free / 1e9:.0f} GB free")
+    N = 29
+    inst = I.large_infinite_n24(3001, N=N)
+    s = hq.Solver.for_instance(inst)
+    with pytest.raises(hq.HQError) as ex:
+        s.solve(tol=1e-10, precision="fp32+df64")
+    assert ex.value.code == hq.HQ_EINVAL
+    rc, st = s.solve(tol=1e-10, precision="fp32+ir", omega=-1.0, order="redblack")
+    assert rc == hq.HQ_OK and st["final_residual"] <= 1e-10, st
+    P = s.stationary()
+    pn, tail = s.layer_marginals()
+    rho, R = s.utilisation(), s.response_pattern()
+    summ = s.summary()
+    s.close()
+    rng = np.random.default_rng(29)
+    B = rng.integers(0, 1 << N, 1500).astype(np.uint64)
+    B[:3] = [0, (1 << N) - 1, (1 << N) - 2]
+    Bi = B.astype(np.int64)
+    nb = np.stack([P[Bi ^ (1 << u)] for u in range(N)], axis=1)
+    lam = inst.lam
+    pq1 = P[-1] * lam / inst.nu.sum()
+    out, inn = oracle.sampled_balance(inst, B, P[Bi], nb, pq1)
+    dev = torch.device("cuda", 0)
+    Pd = torch.as_tensor(P, device=dev)
+    den = 0.0
+    for c0 in range(0, 1 << N, 1 << 26):  # max of P (lambda + mu_B), in chunks
+        y = torch.arange(c0, c0 + (1 << 26), dtype=torch.int64, device=dev)
+        mu = torch.zeros(1 << 26, dtype=torch.float64, device=dev)
+        for u in range(N):
+            mu += ((y >> u) & 1).double() * float(inst.nu[u])
+        den = max(den, float(torch.max(Pd[c0:c0 + (1 << 26)] * (lam + mu))))
+    del Pd
+    assert np.max(np.abs(out - inn)) / den < 1e-10
+    assert abs(P.sum() + tail - 1.0) < 1e-12
+    assert abs(pn.sum() + tail - 1.0) < 1e-12
+    assert np.allclose(R.sum(axis=1), 1.0, rtol=0, atol=1e-10)
+    bound = (1 << (N - 1)) * summ["residual"] * den
+    assert np.max(np.abs(inst.lam_j @ R - inst.nu * rho)) <= bound
