@@ -306,6 +306,7 @@ template <class V>
 struct BlockCtx {
   uint32_t hi, hself;
   int w, n, nbh, par, grp;  // par: list/slot parity; grp: its cp.async group number
+  int it0, size;            // the block's first item and its number of states
   int od, ou;               // byte offsets of the staged blocks' first elements
   typename V::T mu_hi;
 };
@@ -417,6 +418,8 @@ __device__ __forceinline__ void run_items(Smem<V, kWarps, kHP>& s, const SweepAr
     for (int q = lane; q < cu; q += 32) cp_async16(sl + kHalf + 16 * q, gu - ou + 16 * q);
     asm volatile("cp.async.commit_group;" ::: "memory");
     c.grp = ngrp++;
+    c.it0 = __ldg(a.blocks + blk);
+    c.size = s.woff[w + 1] - s.woff[w];
     c.od = od;
     c.ou = ou;
     if (par) bc1 = c;
@@ -442,11 +445,12 @@ __device__ __forceinline__ void run_items(Smem<V, kWarps, kHP>& s, const SweepAr
   // issue every load of item `it` of the block in parity bq
   auto issue = [&](int it, int bq, ItemRef& ir, ItemLoads<V, kNV, kHP>& ld) {
     const BlockCtx<V> c = bq ? bc1 : bc0;
-    const uint2 d = __ldg(a.items + it);
-    ir.cnt = (int)((d.x >> (HQ_SW_HI_BITS + 4)) & 0x1fu) + 1;
+    // items are the block's consecutive runs of 32 states from its first rank
+    const int k32 = (it - c.it0) * HQ_SW_ITEM;
+    ir.cnt = c.size - k32 < HQ_SW_ITEM ? c.size - k32 : HQ_SW_ITEM;
     ir.bq = bq;
     const bool act = lane < ir.cnt;
-    ir.rk = (d.y & ((1u << 27) - 1u)) + (act ? (uint32_t)lane : 0u);
+    ir.rk = c.hself + (uint32_t)k32 + (act ? (uint32_t)lane : 0u);
     const uint32_t rib = ir.rk - c.hself;
     const int n = c.n;
     const int64_t tw = s.tw[n];
