@@ -937,20 +937,29 @@ __global__ void __launch_bounds__(256) k_weights(WeightArgs a, int64_t Sp) {
 // ---- launch ---------------------------------------------------------------------------------
 
 constexpr int kSweepThreads = 512;
+constexpr int kSweepThreadsNarrow = 640;
 constexpr int kSweepThreadsWide = 384;
 
-// One CTA per SM.  FP32 sweeps: 512 threads (16 warps, up to 128 registers); measured at
-// N=24, 384 threads (with two items in flight per warp or one) and 768 threads (spilling)
-// were slower.  FP64 and DF64 sweeps, whose wider values spill at 128 registers: 384
-// threads (12 warps, up to 168 registers); measured at N=24 against 512 and 256, DF64
-// 1.36 vs 1.63 and 1.80 ms per red-black sweep, FP64 1.98 vs 2.00 and 2.21 ms.
-int sweep_threads(int, int kind) { return kind == HQ_PREC_FP32 ? kSweepThreads : kSweepThreadsWide; }
+// One CTA per SM.  FP32 sweeps with the 14-entry high-part list (N <= 24): 640 threads
+// (20 warps, up to 102 registers, 8 bytes of spill); measured at N=24, 0.590 ms per
+// red-black sweep against 0.606 at 576, 0.636 at 512 and 0.702 at 768 threads (spilling),
+// correction sweeps 0.618 against 0.657 at 512.  FP32 sweeps at larger N: 512 threads
+// (their longer lists spill 36-72 bytes at 640).  FP64 and DF64 sweeps, whose wider values
+// spill at 128 registers: 384 threads (12 warps, up to 168 registers); measured at N=24
+// against 512 and 256, DF64 1.36 vs 1.63 and 1.80 ms per red-black sweep, FP64 1.98 vs
+// 2.00 and 2.21 ms.
+int sweep_threads(int H, int kind) {
+  if (kind != HQ_PREC_FP32) return kSweepThreadsWide;
+  return H <= 14 ? kSweepThreadsNarrow : kSweepThreads;
+}
 
 // high-part list sizes: 14 (N <= 24), 18 (N <= 28), 20 (N = 29; no double-float there)
 template <class V, bool kIR>
 const void* sweep_fn(int H) {
-  constexpr int kT = V::kind == HQ_PREC_FP32 ? kSweepThreads : kSweepThreadsWide;
-  if (H <= 14) return (const void*)k_sweep<V, kIR, 14, kT>;
+  constexpr bool k32 = V::kind == HQ_PREC_FP32;
+  constexpr int kT = k32 ? kSweepThreads : kSweepThreadsWide;
+  constexpr int kT14 = k32 ? kSweepThreadsNarrow : kSweepThreadsWide;
+  if (H <= 14) return (const void*)k_sweep<V, kIR, 14, kT14>;
   if (H <= 18) return (const void*)k_sweep<V, kIR, 18, kT>;
   if constexpr (V::kind != HQ_PREC_DF64) return (const void*)k_sweep<V, kIR, 20, kT>;
   return nullptr;
