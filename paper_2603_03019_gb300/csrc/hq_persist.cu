@@ -365,7 +365,7 @@ __device__ __forceinline__ void run_items(Smem<V, kWarps, kHP>& s, const SweepAr
     const int k = r * nwarps + ((r & 1) ? nwarps - 1 - gwarp : gwarp);
     return k < nb ? __ldg(a.perm + b0 + k) : -1;
   };
-  BlockCtx<V> bc0, bc1;  // the held blocks, by parity (selected by value: no local memory)
+  BlockCtx<V> bc;  // the block being worked (its lists and staged blocks alternate parity)
   int ngrp = 0;        // cp.async groups committed so far
   int last_par = 1;    // parity of the most recently set-up block
   // set up block blk in the next parity: returns which held block (0/1) it is
@@ -422,8 +422,7 @@ __device__ __forceinline__ void run_items(Smem<V, kWarps, kHP>& s, const SweepAr
     c.size = s.woff[w + 1] - s.woff[w];
     c.od = od;
     c.ou = ou;
-    if (par) bc1 = c;
-    else bc0 = c;
+    bc = c;
     __syncwarp();  // the lists are visible to the warp
     return par;
   };
@@ -444,7 +443,8 @@ __device__ __forceinline__ void run_items(Smem<V, kWarps, kHP>& s, const SweepAr
   };
   // issue every load of item `it` of the block in parity bq
   auto issue = [&](int it, int bq, ItemRef& ir, ItemLoads<V, kNV, kHP>& ld) {
-    const BlockCtx<V> c = bq ? bc1 : bc0;
+    const BlockCtx<V>& c = bc;
+    (void)bq;
     // items are the block's consecutive runs of 32 states from its first rank
     const int k32 = (it - c.it0) * HQ_SW_ITEM;
     ir.cnt = c.size - k32 < HQ_SW_ITEM ? c.size - k32 : HQ_SW_ITEM;
@@ -479,7 +479,7 @@ __device__ __forceinline__ void run_items(Smem<V, kWarps, kHP>& s, const SweepAr
   };
   // compute item ir from its loads
   auto compute = [&](const ItemRef& ir, const ItemLoads<V, kNV, kHP>& ld) {
-    const BlockCtx<V> c = ir.bq ? bc1 : bc0;
+    const BlockCtx<V>& c = bc;
     // the block's staged low-part blocks: every group up to its own must be complete
     if (ngrp - 1 - c.grp >= 1) asm volatile("cp.async.wait_group 1;" ::: "memory");
     else asm volatile("cp.async.wait_group 0;" ::: "memory");
