@@ -940,28 +940,28 @@ constexpr int kSweepThreads = 512;
 constexpr int kSweepThreadsNarrow = 640;
 constexpr int kSweepThreadsWide = 384;
 
-// One CTA per SM.  FP32 sweeps with the 14-entry high-part list (N <= 24): 640 threads
-// (20 warps, up to 102 registers, 8 bytes of spill); measured at N=24, 0.590 ms per
-// red-black sweep against 0.606 at 576, 0.636 at 512 and 0.702 at 768 threads (spilling),
-// correction sweeps 0.618 against 0.657 at 512.  FP32 sweeps at larger N: 512 threads
-// (their longer lists spill 36-72 bytes at 640).  FP64 and DF64 sweeps, whose wider values
-// spill at 128 registers: 384 threads (12 warps, up to 168 registers); measured at N=24
-// against 512 and 256, DF64 1.36 vs 1.63 and 1.80 ms per red-black sweep, FP64 1.98 vs
-// 2.00 and 2.21 ms.
+// One CTA per SM.  FP32 sweeps with the 14- or 18-entry high-part list (N <= 28): 640
+// threads (20 warps, up to 102 registers, no spills); measured at N=24, 0.562 ms per
+// red-black sweep (0.590 before the item loop held one block context) against 0.606 at
+// 576, 0.636 at 512 and 0.70 at 768 threads (spilling); at N=26 2.28 against 2.54 ms at
+// 512.  FP32 sweeps at N = 29: 512 threads (the 20-entry list spills at 640).  FP64 and
+// DF64 sweeps, whose wider values spill at 128 registers: 384 threads (12 warps, up to 168
+// registers); measured at N=24 against 512 and 256, DF64 1.36 vs 1.63 and 1.80 ms per
+// red-black sweep, FP64 1.98 vs 2.00 and 2.21 ms.
 int sweep_threads(int H, int kind) {
   if (kind != HQ_PREC_FP32) return kSweepThreadsWide;
-  return H <= 14 ? kSweepThreadsNarrow : kSweepThreads;
+  return H <= 18 ? kSweepThreadsNarrow : kSweepThreads;
 }
 
 // high-part list sizes: 14 (N <= 24), 18 (N <= 28), 20 (N = 29; no double-float there)
 template <class V, bool kIR>
 const void* sweep_fn(int H) {
   constexpr bool k32 = V::kind == HQ_PREC_FP32;
-  constexpr int kT = k32 ? kSweepThreads : kSweepThreadsWide;
-  constexpr int kT14 = k32 ? kSweepThreadsNarrow : kSweepThreadsWide;
-  if (H <= 14) return (const void*)k_sweep<V, kIR, 14, kT14>;
+  constexpr int kT = k32 ? kSweepThreadsNarrow : kSweepThreadsWide;
+  constexpr int kT20 = k32 ? kSweepThreads : kSweepThreadsWide;
+  if (H <= 14) return (const void*)k_sweep<V, kIR, 14, kT>;
   if (H <= 18) return (const void*)k_sweep<V, kIR, 18, kT>;
-  if constexpr (V::kind != HQ_PREC_DF64) return (const void*)k_sweep<V, kIR, 20, kT>;
+  if constexpr (V::kind != HQ_PREC_DF64) return (const void*)k_sweep<V, kIR, 20, kT20>;
   return nullptr;
 }
 
