@@ -62,9 +62,11 @@ TRAFFIC_SOURCE = ("ncu --set full of one launch of 2 FP32 red-black sweeps at N=
                   "variant: 640 threads, 14-entry high-part list): 555.3 MB of DRAM traffic for 469.8 MB "
                   "of algorithmic bytes, scaled to this launch by its algorithmic bytes")
 METRIC = "N=24 time-to-1e-10 residual: warm-start+FP32 vs plain FP64; state-updates/s"
-# the plain FP64 sweep's ALU ceiling (fraction of HBM peak), from the measured FP64
-# FMA rate and the sweep's FP64 operations per algorithmic byte; None until measured
-FP64_ALU_CEILING = None
+# the plain FP64 sweep's ALU ceiling: FP64 operations per state update counted by ncu
+# (DFMA + DADD + DMUL thread instructions of two red-black FP64 sweeps at N=22, the same
+# kernel variant), at the FP64 FMA rate measured by `bench.py --fp-rate` on this GPU type
+FP64_OPS_PER_STATE = 46.98
+FP64_RATE = 0.5292e12
 BASE_SEED = {"n29": 3001, "n28": 3001, "n26": 3001, "n24": 3001, "n23": 3001, "n22": 3001, "n20": 2001, "n10": 1001}
 
 
@@ -510,6 +512,8 @@ def run_ours(args):
             ach = b32 / (ms32 / 1000.0) / 1e9
             traffic = (SWEEP_DRAM_PER_ALG_BYTE * 8 * b32 if SWEEP_DRAM_PER_ALG_BYTE else None)
             f64 = per_prec["fp64 redblack"]
+            ceil_ms = FP64_OPS_PER_STATE * (S - 2) / FP64_RATE * 1e3
+            ceil_frac = hq.hq_sweep_bytes(solver.h, hq.HQ_PREC_FP64) / (ceil_ms / 1e3) / 1e9 / peak
             roof = {"bound": "hbm",
                     "kernel": f"k_sweep<FP32>, {args.order} order: one launch = 8 sweeps of layers "
                               "1..N-1 (one grid barrier per phase)",
@@ -519,8 +523,11 @@ def run_ours(args):
                     "bytes_per_launch": 8 * b32, "ms_per_launch": round(8 * ms32, 4),
                     "launches_timed": kern["fp32_sweeps"] // 8,
                     "fp64_sweep": {"achieved": f64["achieved_gbs"], "frac": f64["frac"],
-                                   "alu_ceiling_frac": FP64_ALU_CEILING,
-                                   "note": "plain FP64 sweep, isolated launches of 8 sweeps, red-black"},
+                                   "alu_ceiling_frac": round(ceil_frac, 4),
+                                   "alu_floor_ms_per_sweep": round(ceil_ms, 4),
+                                   "note": "plain FP64 sweep, isolated launches of 8 sweeps, red-black; "
+                                           "ceiling = its algorithmic bytes over the time its FP64 "
+                                           "operations take at the measured FP64 rate"},
                     "refinement_sweeps_in_step": {
                         "ms_per_sweep": round(kern["hi_ms"] / max(1, kern["hi_sweeps"]), 5),
                         "sweeps": kern["hi_sweeps"]},
@@ -548,7 +555,7 @@ def run_ours(args):
                    "omega": "automatic" if args.omega < 0 else args.omega,
                    "order": args.order, "start": "uniform (the paper's)",
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
-                   "l2": "inputs larger than L2 (FP64 table 1.6 GB, FP32 table 0.8 GB)"},
+                   "l2": "inputs larger than L2 (FP64 table 1.8 GB, FP32 table 0.9 GB)"},
         "sweeps_per_step": {"fp32": st0["sweeps_fp32"], "hi": st0["sweeps_hi"]},
         "time_to_tol_ms": compare or None,
         "table_build_ms": st0["ms_table"],
