@@ -96,10 +96,19 @@ template <> struct WT<PolDF> {
 };
 
 // per warp: two block parities x (staged block of layer n-1, staged block of layer n+1),
-// each with 16 bytes of room for the copy's alignment offset
+// each with 16 bytes of room for the copy's alignment offset; then the rank-table entries
+// of the warp's next 32 blocks (kHP + 3 per block, see run_items)
 template <class V>
-constexpr int kSlotBytes() {
+constexpr int kStageBytes() {
   return 4 * (HQ_MAX_BLOCK * (int)sizeof(typename V::T) + 16);
+}
+template <class V, int kHP>
+constexpr int kSlotBytes() {
+  return kStageBytes<V>() + 32 * (kHP + 3) * 4;
+}
+template <class V>
+int slot_bytes(int H) {
+  return H <= 14 ? kSlotBytes<V, 14>() : (H <= 18 ? kSlotBytes<V, 18>() : kSlotBytes<V, 20>());
 }
 
 struct SweepArgs {
@@ -365,6 +374,11 @@ __device__ __forceinline__ void run_items(Smem<V, kWarps, kHP>& s, const SweepAr
   // together: the warp pays one chain of dependent loads (perm, first item, its
   // descriptor) per 32 blocks instead of one per block.  m_id = hi | w << 20 | n << 24 of
   // the lane's block (~0u: none), m_it0 its first item.
+  // The lane also loads its block's rank-table entries into the warp's buffer rhb
+  // (kRHB words per block: the high-part neighbour blocks RH[hi ^ 2^j][w], j < H, then
+  // the block's own rank and those of (hi, w - 1), (hi, w + 1)), all in flight at once.
+  constexpr int kRHB = kHP + 3;
+  uint32_t* rhb = (uint32_t*)(slot + kStageBytes<V>());
   int mbase = -32, m_it0 = 0;
   uint32_t m_id = ~0u;
   auto fetch_meta = [&](int r0) {
@@ -372,17 +386,30 @@ __device__ __forceinline__ void run_items(Smem<V, kWarps, kHP>& s, const SweepAr
     const int r = r0 + lane;
     const int k = r * nwarps + ((r & 1) ? nwarps - 1 - gwarp : gwarp);
     m_id = ~0u;
+    __syncwarp();  // every lane is done with the previous batch's entries
     if (k < nb) {
       m_it0 = __ldg(a.blocks + __ldg(a.perm + b0 + k));
       const uint2 d0 = __ldg(a.items + m_it0);
       m_id = (d0.x & ((1u << (HQ_SW_HI_BITS + 4)) - 1u)) | ((d0.y >> 27) << (HQ_SW_HI_BITS + 4));
+      const uint32_t hi = m_id & ((1u << HQ_SW_HI_BITS) - 1u);
+      const int w = (int)((m_id >> HQ_SW_HI_BITS) & 0xfu);
+      uint32_t* rb = rhb + lane * kRHB;
+      const uint32_t* rh = a.RH + w;
+#pragma unroll
+      for (int j = 0; j < kHP; j++)
+        if (j < H) rb[j] = __ldg(rh + (hi ^ (1u << j)) * (uint32_t)(L + 1));
+      rb[kHP] = __ldg(rh + hi * (uint32_t)(L + 1));
+      rb[kHP + 1] = w >= 1 ? __ldg(rh + hi * (uint32_t)(L + 1) - 1) : 0u;
+      rb[kHP + 2] = w < L ? __ldg(rh + hi * (uint32_t)(L + 1) + 1) : 0u;
     }
+    __syncwarp();
   };
   BlockCtx<V> bc;  // the block being worked (its lists and staged blocks alternate parity)
   int ngrp = 0;        // cp.async groups committed so far
   int last_par = 1;    // parity of the most recently set-up block
-  // set up the block with metadata id (first item it0) in the next parity
-  auto setup = [&](uint32_t id, int it0) -> int {
+  // set up the block with metadata id (first item it0, rank entries at rhb[src]) in the
+  // next parity
+  auto setup = [&](uint32_t id, int it0, int src) -> int {
     const int par = last_par ^ 1;
     last_par = par;
     BlockCtx<V> c;
@@ -395,12 +422,12 @@ __device__ __forceinline__ void run_items(Smem<V, kWarps, kHP>& s, const SweepAr
     const T* p_dn = pv + s.off[n - 1];
     const T* p_up = pv + s.off[n + 1];
     __syncwarp();  // every lane is done with this parity's previous block
-    int idx = -1;
-    if (lane < H) idx = (int)((hi ^ (1u << lane)) * (uint32_t)(L + 1)) + w;
-    else if (lane == 29) idx = (int)(hi * (uint32_t)(L + 1)) + w;
-    else if (lane == 30 && w >= 1) idx = (int)(hi * (uint32_t)(L + 1)) + w - 1;
-    else if (lane == 31 && w < L) idx = (int)(hi * (uint32_t)(L + 1)) + w + 1;
-    const uint32_t rh = idx >= 0 ? __ldg(a.RH + idx) : 0u;
+    const uint32_t* rb = rhb + src * kRHB;
+    uint32_t rh = 0u;
+    if (lane < H) rh = rb[lane];
+    else if (lane == 29) rh = rb[kHP];
+    else if (lane == 30) rh = rb[kHP + 1];
+    else if (lane == 31) rh = rb[kHP + 2];
     c.nbh = __popc(hi);
     T muj = V::zero();
     if (lane < H) {
@@ -448,7 +475,7 @@ __device__ __forceinline__ void run_items(Smem<V, kWarps, kHP>& s, const SweepAr
       if (id == ~0u) return false;  // rounds past the phase's blocks stay past it
       const int it0 = __shfl_sync(kFull, m_it0, src);
       sr++;
-      setup(id, it0);
+      setup(id, it0, src);
       sit = it0;
       sie = it0 + (bc.size + HQ_SW_ITEM - 1) / HQ_SW_ITEM;
       newblk = true;
@@ -598,7 +625,7 @@ __device__ void solve_layer(Smem<V, kWarps, kHP>& s, const SweepArgs& a, int n) 
 template <class V, bool kIR, int kHP, int kThreads>
 __global__ void __launch_bounds__(kThreads, 1) k_sweep(SweepArgs a) {
   constexpr int kWarps = kThreads / 32;
-  constexpr int kSlot = kSlotBytes<V>();
+  constexpr int kSlot = kSlotBytes<V, kHP>();
   extern __shared__ __align__(128) unsigned char smem_dyn[];
   __shared__ Smem<V, kWarps, kHP> s;
   DevScalars* sc = a.sc;
@@ -731,7 +758,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_sweep(SweepArgs a) {
 template <int kHP, int kThreads>
 __global__ void __launch_bounds__(kThreads, 1) k_base_pass(SweepArgs a) {
   constexpr int kWarps = kThreads / 32;
-  constexpr int kSlot = kSlotBytes<PolF64>();
+  constexpr int kSlot = kSlotBytes<PolF64, kHP>();
   extern __shared__ __align__(128) unsigned char smem_dyn[];
   __shared__ Smem<PolF64, kWarps, kHP> s;
   const int N = a.N;
@@ -754,7 +781,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_base_pass(SweepArgs a) {
 template <int kHP, int kThreads>
 __global__ void __launch_bounds__(kThreads, 1) k_residual_fused(SweepArgs a) {
   constexpr int kWarps = kThreads / 32;
-  constexpr int kSlot = kSlotBytes<PolF64>();
+  constexpr int kSlot = kSlotBytes<PolF64, kHP>();
   extern __shared__ __align__(128) unsigned char smem_dyn[];
   __shared__ Smem<PolF64, kWarps, kHP> s;
   const int N = a.N;
@@ -1014,7 +1041,7 @@ template <class V>
 int launch_sweep(hq_solver* h, int nsweeps, cudaEvent_t ev0, cudaEvent_t ev1, int G, bool ir) {
   typedef typename V::T T;
   const int thr = sweep_threads(h->H, V::kind);
-  const size_t smem = (size_t)(thr / 32) * kSlotBytes<V>();
+  const size_t smem = (size_t)(thr / 32) * slot_bytes<V>(h->H);
   const void* kfn = ir ? sweep_fn<PolF32, true>(h->H) : sweep_fn<V, false>(h->H);
   PrecBufs& bp = hq_bufs(h, V::kind);
   SweepArgs a;
@@ -1041,7 +1068,7 @@ template <class V>
 int sweep_grid(hq_solver* h, bool ir, int* G) {
   typedef typename V::T T;
   const int thr = sweep_threads(h->H, V::kind);
-  const size_t smem = (size_t)(thr / 32) * kSlotBytes<V>();
+  const size_t smem = (size_t)(thr / 32) * slot_bytes<V>(h->H);
   const void* kfn = ir ? sweep_fn<PolF32, true>(h->H) : sweep_fn<V, false>(h->H);
   if (!kfn) {
     hq_set_error("no sweep kernel for this precision at this N");
@@ -1107,7 +1134,7 @@ int hq_base_pass(hq_solver* h) {
   a.nu = h->b64.nu;
   a.wv = h->wv64;
   a.out = h->ir;
-  const size_t smem = (size_t)(kSweepThreadsWide / 32) * kSlotBytes<PolF64>();
+  const size_t smem = (size_t)(kSweepThreadsWide / 32) * slot_bytes<PolF64>(h->H);
   const void* kfn = h->H <= 14   ? (const void*)k_base_pass<14, kSweepThreadsWide>
                     : h->H <= 18 ? (const void*)k_base_pass<18, kSweepThreadsWide>
                                  : (const void*)k_base_pass<20, kSweepThreadsWide>;
@@ -1131,7 +1158,7 @@ int hq_residual_fused(hq_solver* h) {
   a.wv = h->wv64;
   HQ_CUDA(cudaMemsetAsync(&h->sc->res_num[0], 0, sizeof(double) * (HQ_MAXN + 1), h->stream));
   HQ_CUDA(cudaMemsetAsync(&h->sc->res_den[0], 0, sizeof(double) * (HQ_MAXN + 1), h->stream));
-  const size_t smem = (size_t)(kSweepThreadsWide / 32) * kSlotBytes<PolF64>();
+  const size_t smem = (size_t)(kSweepThreadsWide / 32) * slot_bytes<PolF64>(h->H);
   const void* kfn = h->H <= 14   ? (const void*)k_residual_fused<14, kSweepThreadsWide>
                     : h->H <= 18 ? (const void*)k_residual_fused<18, kSweepThreadsWide>
                                  : (const void*)k_residual_fused<20, kSweepThreadsWide>;
