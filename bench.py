@@ -57,9 +57,9 @@ DTYPE = {"fp32+ir": "f32 sweeps + f64 refinement base", "fp32+df64": "f32 + df64
 # the bench's launch is too large to capture, so the traffic it reports is this ratio
 # times its algorithmic bytes (traffic grows in proportion to the states swept), and is
 # labelled as extrapolated.  None while no capture of the current kernel exists.
-SWEEP_DRAM_PER_ALG_BYTE = 555.25e6 / 469.76e6
+SWEEP_DRAM_PER_ALG_BYTE = 555.32e6 / 469.76e6
 TRAFFIC_SOURCE = ("ncu --set full of one launch of 2 FP32 red-black sweeps at N=22 (the same kernel "
-                  "variant: 640 threads, 14-entry high-part list): 555.3 MB of DRAM traffic for 469.8 MB "
+                  "variant: 640 threads, 14-entry high-part list, the current code): 555.3 MB of DRAM traffic for 469.8 MB "
                   "of algorithmic bytes, scaled to this launch by its algorithmic bytes")
 METRIC = "N=24 time-to-1e-10 residual: warm-start+FP32 vs plain FP64; state-updates/s"
 # the plain FP64 sweep's ALU ceiling: FP64 operations per state update counted by ncu
