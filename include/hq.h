@@ -99,8 +99,8 @@ typedef struct hq_opts {
                           each finalised layer becomes p_old + omega (p_new - p_old);
                           0 or 1 = Algorithm 1 as printed; (1, 2) fixed; negative =
                           automatic (Young's optimal omega for the contraction rate
-                          observed over the first checks, 90 % of it, at most 1.5,
-                          backed off when the steps stop shrinking).  The fixed point
+                          observed over the second check, at most 1.9, backed off
+                          when the steps stop shrinking).  The fixed point
                           is the same for any omega. */
   int sweep_order;     /* HQ_ORDER_ASCENDING (0): Algorithm 1's order, layers 1..N-1 in
                           turn; HQ_ORDER_REDBLACK (1, not in the paper): all odd layers,

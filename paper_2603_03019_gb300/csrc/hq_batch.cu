@@ -778,12 +778,12 @@ extern "C" int hq_batch_solve(hq_batch* b, const hq_opts* opts_in, hq_stats* sta
       if (!isfinite(step[c]) || (flags & 1u)) status = HQ_EDIVERGED;
       const double ratio = prev[c] > 0.0 ? step[c] / prev[c] : 0.0;
       if (auto_omega) {
-        // as hq_solve: Young's omega for the contraction over the third check, 90 % of its
-        // extrapolation, at most 1.5; halfway back whenever the steps stop shrinking
+        // as hq_solve: Young's omega for the contraction over the second check, at most
+        // 1.9; halfway back whenever the steps stop shrinking
         checks[c]++;
-        if (om[c] == 1.0 && checks[c] == 3 && ratio > 0.0 && ratio < 1.0) {
+        if (om[c] == 1.0 && checks[c] == 2 && ratio > 0.0 && ratio < 1.0) {
           const double r = pow(ratio, 1.0 / nrun);
-          om[c] = fmin(1.0 + 0.9 * (2.0 / (1.0 + sqrt(1.0 - r)) - 1.0), 1.5);
+          om[c] = fmin(2.0 / (1.0 + sqrt(1.0 - r)), 1.9);
         } else if (om[c] > 1.0 && ratio >= 1.0) {
           om[c] = 1.0 + 0.5 * (om[c] - 1.0);
         }
