@@ -952,23 +952,54 @@ __global__ void __launch_bounds__(256) k_weights(WeightArgs a, int64_t Sp) {
     };
     // mu of a neighbour: mu(x) plus or minus one unit's rate
     const double mux = __ldg(a.mulo + (x & ((1u << L) - 1u))) + __ldg(a.muhi + (x >> L));
+    // neighbours four at a time, so their rank-table and table loads are in flight
+    // together; the sums still run in increasing unit order
     if (n < N) {
-      for (int u = 0; u < N; u++) {
-        if ((x >> u) & 1u) continue;
-        const uint32_t y = x | (1u << u);
-        const uint32_t ry = rank(y);
-        const int slot = __popc(x & ((1u << u) - 1u));
-        const double t = a.T[a.toff[n + 1] + (int64_t)ry * a.tw[n + 1] + slot];
-        const double ryv = a.r[a.off[n + 1] + ry];
-        wu += t * (mux + snu[u]) * ryv;
+      uint32_t idle = ~x & ((1u << N) - 1u);
+      while (idle) {
+        int us[4];
+        uint32_t ry[4];
+        double t[4], rv[4];
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+          us[q] = idle ? __ffs(idle) - 1 : -1;
+          idle &= idle - 1u;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; q++)
+          if (us[q] >= 0) ry[q] = rank(x | (1u << us[q]));
+#pragma unroll
+        for (int q = 0; q < 4; q++)
+          if (us[q] >= 0) {
+            const int slot = __popc(x & ((1u << us[q]) - 1u));
+            t[q] = a.T[a.toff[n + 1] + (int64_t)ry[q] * a.tw[n + 1] + slot];
+            rv[q] = a.r[a.off[n + 1] + ry[q]];
+          }
+#pragma unroll
+        for (int q = 0; q < 4; q++)
+          if (us[q] >= 0) wu += t[q] * (mux + snu[us[q]]) * rv[q];
       }
     }
     if (n > 0) {
-      for (int u = 0; u < N; u++) {
-        if (!((x >> u) & 1u)) continue;
-        const uint32_t y = x ^ (1u << u);
-        const uint32_t ry = rank(y);
-        wd += snu[u] * (mux - snu[u]) * a.r[a.off[n - 1] + ry];
+      uint32_t busy = x;
+      while (busy) {
+        int us[4];
+        uint32_t ry[4];
+        double rv[4];
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+          us[q] = busy ? __ffs(busy) - 1 : -1;
+          busy &= busy - 1u;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; q++)
+          if (us[q] >= 0) ry[q] = rank(x ^ (1u << us[q]));
+#pragma unroll
+        for (int q = 0; q < 4; q++)
+          if (us[q] >= 0) rv[q] = a.r[a.off[n - 1] + ry[q]];
+#pragma unroll
+        for (int q = 0; q < 4; q++)
+          if (us[q] >= 0) wd += snu[us[q]] * (mux - snu[us[q]]) * rv[q];
       }
     }
   }
