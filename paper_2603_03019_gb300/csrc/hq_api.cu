@@ -350,7 +350,7 @@ extern "C" int hq_solve(hq_solver* h, const hq_opts* opts_in, hq_stats* stats) {
   if ((o.warm_start == HQ_WARM_MLP || o.warm_start == HQ_WARM_PRODUCT) && h->N >= 2) {
     // the learned (or analytic) start is kept only if it is closer to the fixed point than
     // the paper's uniform start, by the FP64 relative balance residual of Eq. (1) of each
-    // (the judge of the plain iteration's error); no sweep is spent on the test
+    // (the plain iteration's own measure of error); no sweep is spent on the test
     double res_cold = INFINITY, res_warm = INFINITY;
     rc = hq_init_iterate(h, phases[0], nullptr, HQ_HOST);
     if (rc == HQ_OK) rc = hq_compute_residual(h, &res_cold);
