@@ -382,6 +382,18 @@ extern "C" int hq_solve(hq_solver* h, const hq_opts* opts_in, hq_stats* stats) {
   while (!converged && total < o.max_sweeps) {
     const int prec = phases[ph];
     int nrun = o.check_every;
+    // last phase, residual tolerance: when the residual, its step and the per-sweep decay
+    // of the steps predict the tolerance within fewer sweeps than a check, run only
+    // those (and one more) before the next residual evaluation
+    if (ph == nph - 1 && o.tol_kind == HQ_TOL_RESIDUAL && res > 0.0 && res_at_step > 0.0 &&
+        prev_check_step > 0.0 && last_ratio > 0.0 && last_ratio < 1.0) {
+      const double d = pow(last_ratio, 1.0 / o.check_every);
+      const double need = log(0.5 * o.tol * res_at_step / (res * prev_check_step)) / log(d);
+      if (need > 0.0 && need < (double)(o.check_every - 1)) {
+        const int k = (int)ceil(need) + 1;
+        nrun = k < 2 ? 2 : k;
+      }
+    }
     if (nrun > o.max_sweeps - total) nrun = o.max_sweeps - total;
     rc = hq_run_sweeps(h, prec, nrun, h->kev[0], h->kev[1]);
     h->dbg_skip_cta = -1;
@@ -409,7 +421,9 @@ extern "C" int hq_solve(hq_solver* h, const hq_opts* opts_in, hq_stats* stats) {
       status = HQ_EDIVERGED;
       break;
     }
-    const double ratio = prev_check_step > 0.0 ? step / prev_check_step : 0.0;
+    // decay per check of check_every sweeps (a shortened last launch is scaled up to it)
+    double ratio = prev_check_step > 0.0 ? step / prev_check_step : 0.0;
+    if (ratio > 0.0 && nrun != o.check_every) ratio = pow(ratio, (double)o.check_every / nrun);
     const bool last_phase = ph == nph - 1;
     phase_checks++;
     // leave FP32 once its steps stop shrinking geometrically (rounding floor); correction
@@ -433,7 +447,7 @@ extern "C" int hq_solve(hq_solver* h, const hq_opts* opts_in, hq_stats* stats) {
       // against 88 + 24)
       omega_checks++;
       if (h->omega == 1.0 && omega_checks == 2 && ratio > 0.0 && ratio < 1.0) {
-        const double r = pow(ratio, 1.0 / nrun);
+        const double r = pow(ratio, 1.0 / o.check_every);
         const double wopt = 2.0 / (1.0 + sqrt(1.0 - r));
         h->omega = fmin(wopt, 1.9);
       } else if (h->omega > 1.0 && ratio >= 1.0 && !leave && phase_checks > 3) {
