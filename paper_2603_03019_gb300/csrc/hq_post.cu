@@ -356,32 +356,24 @@ __global__ void k_rho_final(int N, int nblk, const long long* partials, const do
   rho[i] = (double)t * 0x1p-61 + summary[5];  // queued states: every unit busy
 }
 
-// h_i[X] = P{B} for B = X with a 0 inserted at bit i (unit i idle), in 64-bit fixed
-// point P 2^61 (P <= 1 and every superset sum <= 1, so the sums are exact integer adds;
-// the quantum 2^-62 is far below the outputs' accuracy)
-__global__ void k_fill_idle(int N, const double* P, long long* zeta) {
-  int64_t half = (int64_t)1 << (N - 1);
-  int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= half * N) return;
-  int i = (int)(g / half);
-  int64_t X = g % half;
-  int64_t y = (X & ((1ll << i) - 1)) | ((X >> i) << (i + 1));
-  zeta[g] = __double2ll_rn(P[y] * 0x1p61);
+// F[B] = P{B} in 64-bit fixed point P 2^61, y-order (P <= 1 and every superset sum of P
+// is <= 1, so the sums are exact integer adds; the quantum 2^-62 is far below the
+// outputs' accuracy)
+__global__ void k_fill_fixed(int64_t S, const double* P, long long* F) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g < S) F[g] = __double2ll_rn(P[g] * 0x1p61);
 }
 
-__device__ __forceinline__ uint32_t squeeze_bit_p(uint32_t x, int u) {
-  return (x & ((1u << u) - 1u)) | ((x >> (u + 1)) << u);
-}
-
-// R[j*N+i] = sum over states with unit i idle and every unit node j prefers to i
-// busy (the superset sum at pre_j(i)), plus waiting calls served by i
-__global__ void k_response(int N, int J, int mode, const uint32_t* pre, const long long* zeta,
+// R[j*N+i] = sum of P over the states with every unit node j prefers to i busy and unit
+// i idle = F[pre] - F[pre + i] with F the superset sums of P (exact integers), plus
+// waiting calls served by i
+__global__ void k_response(int N, int J, int mode, const uint32_t* pre, const long long* F,
                            const double* nu, double nu_sum, const double* summary, double* R) {
   int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= (int64_t)J * N) return;
   int i = (int)(g % N);
-  int64_t half = (int64_t)1 << (N - 1);
-  double v = (double)zeta[(int64_t)i * half + squeeze_bit_p(pre[g], i)] * 0x1p-61;
+  const uint32_t m = pre[g];
+  double v = (double)(F[m] - F[m | (1u << i)]) * 0x1p-61;
   if (mode != HQ_LOSS) v += summary[2] * nu[i] / nu_sum;
   R[g] = v;
 }
@@ -535,18 +527,13 @@ int hq_finalize(hq_solver* h, int prec, bool full_outputs, double* residual_out)
     HQ_LAUNCHED();
     k_rho_final<<<1, 32, 0, h->stream>>>(h->N, nblk, (const long long*)h->partials, h->summary, h->rho);
     HQ_LAUNCHED();
-    if (h->N >= 2) {
-      int64_t half = (int64_t)1 << (h->N - 1);
-      k_fill_idle<<<(unsigned)((half * h->N + 255) / 256), 256, 0, h->stream>>>(h->N, h->P,
-                                                                               (long long*)h->zeta);
-      HQ_LAUNCHED();
-      rc = hq_zeta_subset(h, (long long*)h->zeta, h->N - 1, h->N, true);
-      if (rc != HQ_OK) return rc;
-    } else {
-      // one unit: the only idle state is B = 0
-      k_fill_idle<<<1, 32, 0, h->stream>>>(1, h->P, (long long*)h->zeta);
-      HQ_LAUNCHED();
-    }
+    // one superset-sum transform of P over all N bits (in the transform scratch, which
+    // holds N 2^(N-1) >= 2^N values): every response probability is a difference of two
+    // of its entries
+    k_fill_fixed<<<(unsigned)((h->S + 255) / 256), 256, 0, h->stream>>>(h->S, h->P, (long long*)h->zeta);
+    HQ_LAUNCHED();
+    rc = hq_zeta_subset(h, (long long*)h->zeta, h->N, 1, true);
+    if (rc != HQ_OK) return rc;
     int64_t jn = (int64_t)h->J * h->N;
     k_response<<<(unsigned)((jn + 255) / 256), 256, 0, h->stream>>>(
         h->N, h->J, h->mode, h->pre, (const long long*)h->zeta, h->nu, h->nu_sum, h->summary, h->R);
