@@ -270,8 +270,7 @@ extern "C" int hq_load(hq_solver* h, const double* lambda_j, const double* nu, c
   if (rc != HQ_OK) return rc;
   rc = hq_build_weights(h);
   if (rc != HQ_OK) return rc;
-  rc = hq_convert_tables(h);
-  if (rc != HQ_OK) return rc;
+  h->df_ready = false;
   HQ_CUDA(cudaStreamSynchronize(h->stream));
   h->ms_table = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   h->loaded = true;
@@ -335,6 +334,11 @@ extern "C" int hq_solve(hq_solver* h, const hq_opts* opts_in, hq_stats* stats) {
     case HQ_PREC_FP32_IR: phases[0] = HQ_PREC_FP32; phases[1] = HQ_PREC_IRC; nph = 2; break;
     default: phases[0] = HQ_PREC_FP32; phases[1] = HQ_PREC_FP64; nph = 2; break;
   }
+  for (int q = 0; q < nph; q++)
+    if (phases[q] == HQ_PREC_DF64) {
+      const int rcd = hq_ensure_df(h);
+      if (rcd != HQ_OK) return rcd;
+    }
   int rebases = 0, ir_bases = 0, ir_flat = 0, fp32_flat = 0;
   double step_base = 0.0;  // the first step of the current refinement base
   double last_ratio = 0.0;  // the step decay of the check before
@@ -721,6 +725,10 @@ extern "C" int hq_profile_sweep(hq_solver* h, int precision, int sweeps, float* 
   if (precision == HQ_PREC_DF64 && !h->bdf.T) {
     hq_set_error("double-float precisions are not kept above N = 28 (memory)");
     return HQ_EINVAL;
+  }
+  if (precision == HQ_PREC_DF64) {
+    rc = hq_ensure_df(h);
+    if (rc != HQ_OK) return rc;
   }
   if (precision == HQ_PREC_FP32_IR) precision = HQ_PREC_IRC;  // correction sweeps
   if (h->cur_prec != precision) {

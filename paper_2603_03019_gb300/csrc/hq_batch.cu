@@ -467,6 +467,7 @@ extern "C" int hq_batch_create(hq_solver* const* solvers, int count, void* strea
     if (solvers[c]->N < 2) { hq_set_error("batched solvers need N >= 2"); return HQ_EINVAL; }
     if (solvers[c]->N > HQ_DF_MAXN) { hq_set_error("batched solvers need N <= 28"); return HQ_EINVAL; }
   }
+
   hq_batch* b = new hq_batch();
   b->K = count;
   b->s.assign(solvers, solvers + count);
@@ -651,7 +652,10 @@ extern "C" int hq_batch_tune(hq_batch* b, int precision, int sweeps, int* varian
     return HQ_EINVAL;
   }
   if (sweeps < 1) sweeps = 1;
-  int rc = on_batch_stream(b, [&](hq_solver* h) { return hq_init_iterate(h, precision, nullptr, HQ_HOST); });
+  // the double-float tables (made lazily after each load), on the batch's stream
+  int rc = on_batch_stream(b, [&](hq_solver* h) { return hq_ensure_df(h); });
+  if (rc != HQ_OK) return rc;
+  rc = on_batch_stream(b, [&](hq_solver* h) { return hq_init_iterate(h, precision, nullptr, HQ_HOST); });
   if (rc != HQ_OK) return rc;
   std::vector<int> act(b->K, 1);
   std::vector<double> om1(b->K, 1.0);
@@ -712,6 +716,11 @@ extern "C" int hq_batch_solve(hq_batch* b, const hq_opts* opts_in, hq_stats* sta
   if (!(o.omega < 2.0) || (o.omega >= 0.0 && o.omega < 1.0 && o.omega != 0.0)) {
     hq_set_error("omega must be 0, in [1, 2), or negative (automatic)");
     return HQ_EINVAL;
+  }
+  {
+    // the double-float tables (made lazily after each load), on the batch's stream
+    const int rcd = on_batch_stream(b, [&](hq_solver* h) { return hq_ensure_df(h); });
+    if (rcd != HQ_OK) return rcd;
   }
   const bool auto_omega = o.omega < 0.0;
   const double stall = o.fp32_stall > 0.0 ? o.fp32_stall : 0.9;

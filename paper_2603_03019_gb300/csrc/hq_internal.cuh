@@ -272,6 +272,7 @@ struct hq_solver {
   unsigned spin_limit = 0;     // bounded waits of the sweep kernel (0: the default)
   int dbg_skip_cta = -1;       // fault injection: this CTA skips one barrier arrival
   cudaEvent_t kev[2] = {nullptr, nullptr};  // brackets of each sweep launch in hq_solve
+  bool df_ready = false;       // the double-float table matches the current instance
   void* wv64 = nullptr;        // per-state weights (w'', v'') in FP64 (double2, layer-ranked)
   void* wv32 = nullptr;        // the same in FP32 (float2)
   double* mutab = nullptr;     // mu of a low part (2^L entries), then of a high part (2^H)
@@ -344,7 +345,9 @@ int hq_sweep_item_list(int N, int order, std::vector<uint2>& items, std::vector<
 int hq_build_items(hq_solver* h);     // at hq_create, after the layout
 int hq_build_weights(hq_solver* h);   // at hq_load, after the table and r (hq_persist.cu)
 int hq_iter_sums(hq_solver* h, int prec, const void* p, double* dst);  // 4 layer sums -> dst[4][N+1] (device)
-int hq_convert_tables(hq_solver* h);  // at hq_load: FP32 and DF64 copies of the table
+// the double-float copy of the table, made on the first use of a double-float precision
+// after each hq_load (the FP32 copy is written with the FP64 table)
+int hq_ensure_df(hq_solver* h);
 
 // table (hq_table.cu)
 int hq_build_table(hq_solver* h);

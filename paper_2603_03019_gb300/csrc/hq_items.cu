@@ -54,12 +54,10 @@ __global__ void k_lidx(int L, int64_t Sp, const uint32_t* masks, const uint32_t*
   for (int q = 0; q < 3; q++) lidx[(int64_t)q * Sp + g] = wd[q];
 }
 
-__global__ void k_table_conv(int64_t n, const double* T64, float* T32, float2* Tdf) {
+__global__ void k_table_conv(int64_t n, const double* T64, float2* Tdf) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const double v = T64[i];
-  T32[i] = (float)v;
-  if (Tdf) Tdf[i] = df_from_double(v);
+  Tdf[i] = df_from_double(T64[i]);
 }
 
 }  // namespace
@@ -217,11 +215,14 @@ int hq_build_items(hq_solver* h) {
   return HQ_OK;
 }
 
-int hq_convert_tables(hq_solver* h) {
+int hq_ensure_df(hq_solver* h) {
+  if (h->df_ready || !h->bdf.T) return HQ_OK;
   const int64_t n = h->tentries;
-  if (n == 0) return HQ_OK;
-  k_table_conv<<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(n, (const double*)h->b64.T,
-                                                                    (float*)h->b32.T, (float2*)h->bdf.T);
-  HQ_LAUNCHED();
+  if (n > 0) {
+    k_table_conv<<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(n, (const double*)h->b64.T,
+                                                                      (float2*)h->bdf.T);
+    HQ_LAUNCHED();
+  }
+  h->df_ready = true;
   return HQ_OK;
 }

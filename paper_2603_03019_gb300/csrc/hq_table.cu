@@ -170,9 +170,10 @@ struct EmitArgs {
   int64_t tw[HQ_MAXN + 1];    // record width (state-major layout, HQ_TW)
 };
 
-// one thread per state of layers 1..N: slot s <- F_{c_s}(m - c_s) / scale
+// one thread per state of layers 1..N: slot s <- F_{c_s}(m - c_s) / scale, in FP64 and
+// its FP32 copy
 __global__ void k_emit(EmitArgs a, int64_t S, const uint32_t* masks, const long long* zeta, double inv_scale,
-                       double* T64) {
+                       double* T64, float* T32) {
   int64_t g = a.off[1] + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= S) return;
   int n = 1;
@@ -185,7 +186,9 @@ __global__ void k_emit(EmitArgs a, int64_t S, const uint32_t* masks, const long 
   int s = 0;
   for (uint32_t y = x; y; y &= y - 1, s++) {
     int u = __ffs(y) - 1;
-    T64[rec + s] = (double)__ldg(zeta + (int64_t)u * half + squeeze_bit(x, u)) * inv_scale;
+    const double v = (double)__ldg(zeta + (int64_t)u * half + squeeze_bit(x, u)) * inv_scale;
+    T64[rec + s] = v;
+    T32[rec + s] = (float)v;
   }
 }
 
@@ -217,7 +220,7 @@ int hq_build_table(hq_solver* h) {
   }
   int64_t cnt = h->Sp - h->off[1];
   k_emit<<<(unsigned)((cnt + 255) / 256), 256, 0, h->stream>>>(
-      a, h->Sp, h->masks, z, 1.0 / scale, (double*)h->b64.T);
+      a, h->Sp, h->masks, z, 1.0 / scale, (double*)h->b64.T, (float*)h->b32.T);
   HQ_LAUNCHED();
   return HQ_OK;
 }
