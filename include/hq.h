@@ -273,7 +273,8 @@ int hq_dispatch_table_static(int N, int J, const double* lambda_j, const int32_t
  * so that small instances, whose per-layer work cannot fill the GPU, share it.
  *
  * hq_batch_create: solvers[0..count-1] are loaded solvers (hq_load succeeded, N >= 2)
- *   on the current device; they are borrowed (not owned) and must outlive the batch.
+ *   on the current device; they are borrowed (not owned) and must outlive the batch; a
+ *   solver may be loaded with another instance (hq_load) between batched calls.
  *   stream: a cudaStream_t, or NULL for a stream of the batch's own.  Builds the
  *   combined work lists (host memory for the build, device memory for the lists).
  *   Errors: HQ_EINVAL (NULL, count < 1, N < 2, another device), HQ_ESTATE (a solver not

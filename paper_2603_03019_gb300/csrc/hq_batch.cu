@@ -455,6 +455,25 @@ int on_batch_stream(hq_batch* b, F fn) {
   return rc;
 }
 
+// A solver of the batch may have been loaded with another instance of its size since the
+// batch was made: bring the per-instance total rate (the one value of an instance the
+// batch keeps by value) up to date, and make the double-float tables, on the batch's
+// stream.
+int refresh_instances(hq_batch* b) {
+  bool stale = false;
+  for (int c = 0; c < b->K; c++)
+    if (b->hcfg[c].lam != b->s[c]->lam) {
+      b->hcfg[c].lam = b->s[c]->lam;
+      stale = true;
+    }
+  if (stale) {
+    HQ_CUDA(cudaMemcpyAsync(b->cfg, b->hcfg.data(), sizeof(BCfg) * b->hcfg.size(), cudaMemcpyHostToDevice,
+                            b->stream));
+    HQ_CUDA(cudaStreamSynchronize(b->stream));
+  }
+  return on_batch_stream(b, [&](hq_solver* h) { return hq_ensure_df(h); });
+}
+
 }  // namespace
 
 extern "C" int hq_batch_create(hq_solver* const* solvers, int count, void* stream, hq_batch** out) {
@@ -652,8 +671,7 @@ extern "C" int hq_batch_tune(hq_batch* b, int precision, int sweeps, int* varian
     return HQ_EINVAL;
   }
   if (sweeps < 1) sweeps = 1;
-  // the double-float tables (made lazily after each load), on the batch's stream
-  int rc = on_batch_stream(b, [&](hq_solver* h) { return hq_ensure_df(h); });
+  int rc = refresh_instances(b);
   if (rc != HQ_OK) return rc;
   rc = on_batch_stream(b, [&](hq_solver* h) { return hq_init_iterate(h, precision, nullptr, HQ_HOST); });
   if (rc != HQ_OK) return rc;
@@ -718,9 +736,8 @@ extern "C" int hq_batch_solve(hq_batch* b, const hq_opts* opts_in, hq_stats* sta
     return HQ_EINVAL;
   }
   {
-    // the double-float tables (made lazily after each load), on the batch's stream
-    const int rcd = on_batch_stream(b, [&](hq_solver* h) { return hq_ensure_df(h); });
-    if (rcd != HQ_OK) return rcd;
+    const int rcr = refresh_instances(b);
+    if (rcr != HQ_OK) return rcr;
   }
   const bool auto_omega = o.omega < 0.0;
   const double stall = o.fp32_stall > 0.0 ? o.fp32_stall : 0.9;

@@ -72,6 +72,28 @@ def test_batch_matches_oracle(gpu_lib, prec, tol, omega):
         assert st["final_residual"] < 1e-10
 
 
+def test_batch_after_reloading_its_solvers(gpu_lib):
+    """The solvers of a batch are loaded with other instances of the same sizes after the
+    batch was made (the double-float tables are made on first use after every load): a
+    double-float batched solve then matches the oracle on the new instances."""
+    first = _instances()
+    second = _instances(load=0.5)
+    solvers = [hq.Solver.for_instance(i) for i in first]
+    b = hq.hq_batch_create([s.h for s in solvers])
+    rc, stats, _ = hq.hq_batch_solve(b, len(first), _opts("fp32+df64", 1e-13))
+    assert rc == hq.HQ_OK
+    for s, inst in zip(solvers, second):
+        s.load(inst.lam_j, inst.nu, inst.pref)
+    rc, stats, _ = hq.hq_batch_solve(b, len(second), _opts("df64", 1e-13))
+    assert rc == hq.HQ_OK, stats
+    for s, inst in zip(solvers, second):
+        r = oracle.solve(inst, eps=1e-15)
+        assert np.max(np.abs(s.stationary() - r["P"])) < 1e-10, inst.name
+    hq.hq_batch_destroy(b)
+    for s in solvers:
+        s.close()
+
+
 def test_batch_independent_of_company(gpu_lib):
     """FP64: an instance's result does not depend on the other instances of its batch."""
     insts = _instances()
