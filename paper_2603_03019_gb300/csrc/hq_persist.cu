@@ -321,15 +321,18 @@ struct BlockCtx {
 };
 struct ItemRef {
   uint32_t rk;  // this lane's state rank in layer n
-  int cnt, bq;  // states in the item; which held block (0/1) it belongs to
+  int cnt, bq;  // states in the item; the parity of its block's lists and staged blocks
 };
 
 // Process the rank blocks [b0, b1) of a phase whose layers start at f (li = (n - f) >>
 // order).  The phase's blocks come by decreasing cost (a.perm) and go to the warps in
 // snake order: round r gives block r W + g (r even) or r W + W - 1 - g (r odd) to warp g,
-// so the warps' totals even out.  A warp walks its blocks' items in order: per item it
-// issues every load (table record, high-part neighbours, r, the old value, the weights)
-// and then computes.  A block's neighbour lists and staged low-part blocks alternate
+// so the warps' totals even out.  The metadata of 32 rounds (each block's first item,
+// descriptor and rank-table entries) is fetched at once, one block per lane.  A warp
+// walks its blocks' items in order: per item it issues every load (table record,
+// high-part neighbours, r, the old value, the weights) and then computes; the
+// high-part neighbours must be loaded with the rest (loading them inside the gather was
+// measured 1.5x slower).  A block's neighbour lists and staged low-part blocks alternate
 // between two parities.  One lane per state of an item.
 // kMode 0: a sweep (write p, add the layer sums into s.ws);  kMode 1: a correction
 // sweep (the iterate is e, base terms from a.ir);  kMode 2: the base pass of the
