@@ -305,3 +305,19 @@ def test_sampled_balance_matches_table_route():
     pq1 = P[-1] * inst.lam / inst.nu.sum()
     out, inn = oracle.sampled_balance(inst, B, P[B.astype(np.int64)], nb, pq1)
     assert np.max(np.abs(out - inn)) / np.max(out) < 1e-13
+
+
+def test_openmp_build_matches_the_plain_one():
+    """The OpenMP build of the oracle (the loops over a layer's states on all host
+    threads; only the order of the layer sums changes) gives the plain build's solution
+    to rounding, and the residual-stopped solve used for timing reaches its tolerance."""
+    import oracle as O
+
+    inst = I.geometric_instance(12, 40, 31, 0.6, nu_lo=0.5, nu_hi=1.5, mode=2)
+    a = O.solve(inst, eps=1e-14, threads=1)
+    b = O.solve(inst, eps=1e-14, threads=0)
+    assert a["sweeps"] == b["sweeps"]
+    for k in ("P", "rho", "R", "W", "pn"):
+        assert np.max(np.abs(a[k] - b[k])) < 1e-13, k
+    r = O.solve_to_residual(inst, 1e-10, threads=0)
+    assert r["converged"] and r["residual"] <= 1e-10 and r["sweeps"] % 8 == 0
