@@ -117,8 +117,11 @@ def _load(threads: int = 1):
             "or_des_loss": (_i, [_i, _i, _pd, _pd, _pi32, _pd, _i, _i64, _i64, _i64, ctypes.c_uint64,
                                  _pd, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
                                  _pd, _pd]),
-            "or_des_service": (_d, [_i, _d, ctypes.c_uint64, ctypes.c_uint64]),
-            "or_des_uniform": (_d, [ctypes.c_uint64, _i64, ctypes.c_uint64]),
+            "or_des_service": (ctypes.c_float, [_i, ctypes.c_float, ctypes.c_uint64, ctypes.c_uint64]),
+            "or_des_uniform": (ctypes.c_float, [ctypes.c_uint64, _i64, ctypes.c_uint64]),
+            "or_des_ln": (ctypes.c_float, [ctypes.c_float]),
+            "or_des_exp": (ctypes.c_float, [ctypes.c_float]),
+            "or_des_cos2pi": (ctypes.c_float, [ctypes.c_float]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)

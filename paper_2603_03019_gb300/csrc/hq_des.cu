@@ -17,10 +17,15 @@
 // Random numbers come from one counter-based generator so that each replication's
 // stream does not depend on scheduling: x = F(key_r + (c + 1) gamma) with F the
 // splitmix64 finaliser (Steele, Lea & Flood, OOPSLA 2014), gamma = 0x9e3779b97f4a7c15,
-// key_r = F(seed + (r + 1) gamma), u = ((x >> 11) + 1) 2^-53 in (0, 1]; draw c = 8 a + k
-// of arrival a: k = 0 inter-arrival time, 1 node, 2..6 service time.  Every FP64 step
-// is written with explicit round-to-nearest operations (no contraction into FMA), so the
-// trajectory depends only on the math functions' last-bit rounding.
+// key_r = F(seed + (r + 1) gamma); draw c = 8 a + k of arrival a: k = 0 inter-arrival
+// time, 1 node, 2..6 service time.  The node's uniform is ((x >> 11) + 1) 2^-53 in
+// (0, 1]; the variates' are ((x >> 40) + 1) 2^-24, exact in FP32.
+//
+// The variates are FP32 (their relative rounding, about 1e-7, is far below any
+// statistical effect), built with a logarithm, an exponential and a cosine written here
+// from their series, every step one explicit round-to-nearest operation; the clock and
+// the sums are FP64.  On this GPU the FP32 pipe is many times faster than the FP64 one,
+// and the same steps in the CPU oracle give every replication the same trajectory.
 #include "hq_internal.cuh"
 
 namespace {
@@ -35,39 +40,120 @@ __device__ __forceinline__ uint64_t des_mix(uint64_t z) {
   return z ^ (z >> 31);
 }
 
-__device__ __forceinline__ double des_u(uint64_t key, uint64_t c) {
+__device__ __forceinline__ double des_u53(uint64_t key, uint64_t c) {
   const uint64_t x = des_mix(key + (c + 1) * kGamma);
   return __dmul_rn((double)((x >> 11) + 1), 0x1.0p-53);
 }
 
-__device__ __forceinline__ double des_normal(double u1, double u2) {
-  const double two_pi = 6.283185307179586476925286766559;
-  return __dmul_rn(sqrt(__dmul_rn(-2.0, log(u1))), cos(__dmul_rn(two_pi, u2)));
+__device__ __forceinline__ float des_u24(uint64_t key, uint64_t c) {
+  const uint64_t x = des_mix(key + (c + 1) * kGamma);
+  return __fmul_rn((float)((x >> 40) + 1), 0x1.0p-24f);
 }
 
-__device__ double des_service(int kind, double m, uint64_t key, uint64_t c0) {
-  const double u2 = des_u(key, c0), u3 = des_u(key, c0 + 1);
+// a * b + c with two roundings (never contracted into one FMA)
+__device__ __forceinline__ float mad2(float a, float b, float c) { return __fadd_rn(__fmul_rn(a, b), c); }
+
+// ln x for a positive normal x: x = m 2^e, m in [sqrt(1/2), sqrt(2)), ln m = 2 atanh(s)
+// = 2 (s + s^3/3 + s^5/5 + s^7/7 + s^9/9), s = (m - 1)/(m + 1); e ln 2 by Cody and Waite's
+// split (a 16-bit high part, so its product with e is exact)
+__device__ float des_ln(float x) {
+  const uint32_t b = __float_as_uint(x);
+  int e = (int)((b >> 23) & 0xffu) - 127;
+  float m = __uint_as_float((b & 0x7fffffu) | 0x3f800000u);
+  if (m > 0x1.6a09e6p+0f) {
+    m = __fmul_rn(m, 0.5f);
+    e += 1;
+  }
+  const float s = __fdiv_rn(__fsub_rn(m, 1.0f), __fadd_rn(m, 1.0f));
+  const float z = __fmul_rn(s, s);
+  float q = 0x1.c71c72p-4f;
+  q = mad2(q, z, 0x1.24924ap-3f);
+  q = mad2(q, z, 0x1.99999ap-3f);
+  q = mad2(q, z, 0x1.555556p-2f);
+  q = mad2(q, z, 1.0f);
+  const float lnm = __fmul_rn(__fadd_rn(s, s), q);
+  const float ef = (float)e;
+  const float lo = mad2(ef, 0x1.7f7d1cp-20f, lnm);
+  return mad2(ef, 0x1.62e4p-1f, lo);
+}
+
+// e^y: y = k ln 2 + r, |r| <= ln2 / 2, e^r from its Taylor series to r^8 / 8!
+__device__ float des_exp(float y) {
+  const float k = floorf(mad2(y, 0x1.715476p+0f, 0.5f));
+  float r = __fsub_rn(y, __fmul_rn(k, 0x1.62e4p-1f));
+  r = __fsub_rn(r, __fmul_rn(k, 0x1.7f7d1cp-20f));
+  float p = 0x1.a01a02p-16f;
+  p = mad2(p, r, 0x1.a01a02p-13f);
+  p = mad2(p, r, 0x1.6c16c2p-10f);
+  p = mad2(p, r, 0x1.111112p-7f);
+  p = mad2(p, r, 0x1.555556p-5f);
+  p = mad2(p, r, 0x1.555556p-3f);
+  p = mad2(p, r, 0.5f);
+  p = mad2(p, r, 1.0f);
+  p = mad2(p, r, 1.0f);
+  return __fmul_rn(p, __uint_as_float((uint32_t)((int)k + 127) << 23));
+}
+
+// cos(2 pi u), u in [0, 1]: symmetries to w in [0, 1/4]; the Taylor series of cos (angle
+// <= pi/4, to a^10 / 10!) or of the sine of the complement (to b^9 / 9!)
+__device__ float des_cos2pi(float u) {
+  float v = u;
+  if (v > 0.5f) v = __fsub_rn(1.0f, v);
+  float sign = 1.0f;
+  if (v > 0.25f) {
+    v = __fsub_rn(0.5f, v);
+    sign = -1.0f;
+  }
+  float c;
+  if (v <= 0.125f) {
+    const float a = __fmul_rn(0x1.921fb6p+2f, v);
+    const float a2 = __fmul_rn(a, a);
+    float p = -0x1.27e4fcp-22f;
+    p = mad2(p, a2, 0x1.a01a02p-16f);
+    p = __fsub_rn(__fmul_rn(p, a2), 0x1.6c16c2p-10f);
+    p = mad2(p, a2, 0x1.555556p-5f);
+    p = __fsub_rn(__fmul_rn(p, a2), 0.5f);
+    c = mad2(p, a2, 1.0f);
+  } else {
+    const float bb = __fmul_rn(0x1.921fb6p+2f, __fsub_rn(0.25f, v));
+    const float b2 = __fmul_rn(bb, bb);
+    float p = 0x1.71de3ap-19f;
+    p = __fsub_rn(__fmul_rn(p, b2), 0x1.a01a02p-13f);
+    p = mad2(p, b2, 0x1.111112p-7f);
+    p = __fsub_rn(__fmul_rn(p, b2), 0x1.555556p-3f);
+    p = mad2(p, b2, 1.0f);
+    c = __fmul_rn(bb, p);
+  }
+  return __fmul_rn(sign, c);
+}
+
+__device__ __forceinline__ float des_normal(float u1, float u2) {
+  return __fmul_rn(__fsqrt_rn(__fmul_rn(-2.0f, des_ln(u1))), des_cos2pi(u2));
+}
+
+__device__ float des_service(int kind, float m, uint64_t key, uint64_t c0) {
+  const float u2 = des_u24(key, c0), u3 = des_u24(key, c0 + 1);
   switch (kind) {
     case 0:
-      return __dmul_rn(-m, log(u2));
+      return __fmul_rn(-m, des_ln(u2));
     case 1: {
-      const double s2 = log(2.0);
-      const double mu = __dsub_rn(log(m), __dmul_rn(0.5, s2));
-      return exp(__dadd_rn(mu, __dmul_rn(sqrt(s2), des_normal(u2, u3))));
+      const float s2 = 0x1.62e43p-1f;  // ln 2: the exponential's variance
+      const float mu = __fsub_rn(des_ln(m), __fmul_rn(0.5f, s2));
+      return des_exp(__fadd_rn(mu, __fmul_rn(__fsqrt_rn(s2), des_normal(u2, u3))));
     }
     case 2: {
-      double prod = __dmul_rn(u2, u3);
-      prod = __dmul_rn(prod, des_u(key, c0 + 2));
-      prod = __dmul_rn(prod, des_u(key, c0 + 3));
-      prod = __dmul_rn(prod, des_u(key, c0 + 4));
-      return __dmul_rn(-__ddiv_rn(m, 5.0), log(prod));
+      float prod = __fmul_rn(u2, u3);
+      prod = __fmul_rn(prod, des_u24(key, c0 + 2));
+      prod = __fmul_rn(prod, des_u24(key, c0 + 3));
+      prod = __fmul_rn(prod, des_u24(key, c0 + 4));
+      return __fmul_rn(-__fdiv_rn(m, 5.0f), des_ln(prod));
     }
     case 3: {
-      const double z = des_normal(u2, u3);
-      return __dmul_rn(m, __dmul_rn(z, z));
+      const float z = des_normal(u2, u3);
+      return __fmul_rn(m, __fmul_rn(z, z));
     }
     default:
-      return __dmul_rn(__dmul_rn(2.0, m), u2);
+      return __fmul_rn(__fmul_rn(2.0f, m), u2);
   }
 }
 
@@ -101,6 +187,7 @@ __global__ void __launch_bounds__(kDesThreads) k_des_loss(DesArgs a) {
   if (r >= a.reps) return;
   const int N = a.N, J = a.J;
   const double lam = __ldg(a.cdf + J - 1);
+  const float lamf = __double2float_rn(lam);
   const uint64_t key = des_mix(a.seed + (uint64_t)(r + 1) * kGamma);
   double fr[kDesMaxN], busy[kDesMaxN];
   int64_t served[kDesMaxN];
@@ -113,14 +200,14 @@ __global__ void __launch_bounds__(kDesThreads) k_des_loss(DesArgs a) {
   double resp = 0.0, t = 0.0, t0 = 0.0;
   for (int64_t k = 0; k < a.arrivals; k++) {
     const uint64_t c = 8 * (uint64_t)k;
-    t = __dadd_rn(t, __ddiv_rn(-log(des_u(key, c)), lam));
+    t = __dadd_rn(t, (double)__fdiv_rn(-des_ln(des_u24(key, c)), lamf));
     const bool in_window = k >= a.warmup;
     if (k == a.warmup) {
       t0 = t;
       for (int i = 0; i < N; i++)
         if (fr[i] > t0) busy[i] = __dsub_rn(fr[i], t0);
     }
-    const double target = __dmul_rn(des_u(key, c + 1), lam);
+    const double target = __dmul_rn(des_u53(key, c + 1), lam);
     int lo = 0, hi = J - 1;
     while (lo < hi) {
       const int mid = (lo + hi) / 2;
@@ -140,7 +227,7 @@ __global__ void __launch_bounds__(kDesThreads) k_des_loss(DesArgs a) {
       if (in_window) lost++;
       continue;
     }
-    const double s = des_service(a.kind, __ddiv_rn(1.0, __ldg(a.nu + unit)), key, c + 2);
+    const double s = (double)des_service(a.kind, __double2float_rn(__ddiv_rn(1.0, __ldg(a.nu + unit))), key, c + 2);
     fr[unit] = __dadd_rn(t, s);
     if (in_window) {
       busy[unit] = __dadd_rn(busy[unit], s);

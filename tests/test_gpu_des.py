@@ -17,9 +17,9 @@ KINDS = ["exponential", "lognormal", "gamma5", "gamma05", "uniform"]
 
 @pytest.mark.parametrize("kind", KINDS)
 def test_replications_match_the_oracle(gpu_lib, kind):
-    """Same seed, same counter-based streams, same arithmetic order: every replication's
-    integer counts are equal and its times agree to rounding (the math functions' last
-    bit is all that may differ)."""
+    """Same seed, same counter-based streams, the same IEEE steps for every variate (the
+    FP32 series functions are written out on both sides): every replication's integer
+    counts are equal and its times agree to rounding."""
     inst = I.des_instance(4242, N=10, load=0.7)
     tt = I.travel_times(inst)
     reps, arr, warm, seed = 40, 20_000, 500, 99

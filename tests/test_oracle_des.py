@@ -116,3 +116,28 @@ def test_uniforms_are_in_the_open_unit_interval_and_independent_of_schedule():
     c = [lib.or_des_uniform(9, 4, c) for c in range(1000)]
     assert a != c
     assert abs(np.mean(a) - 0.5) < 5 * math.sqrt(1 / 12 / 1000)
+
+
+def test_series_functions_are_accurate():
+    """The FP32 logarithm, exponential and cosine the simulation forms its variates with,
+    against numpy's FP64 functions over their whole input ranges: ln over the uniforms'
+    range (2^-120, 1] and the means, e^y for |y| <= 20, cos(2 pi u) on [0, 1].  A dropped
+    series term or a wrong constant costs orders of magnitude more than these bounds."""
+    lib = oracle._load(1)
+    r = np.random.default_rng(5)
+    xs = np.concatenate([np.exp2(-r.uniform(0, 120, 4000)), r.uniform(0, 1, 4000), r.uniform(0.05, 20, 500),
+                         [2.0 ** -24, 0.5, 1.0, np.sqrt(0.5), np.sqrt(2.0)]]).astype(np.float32)
+    ln = np.array([lib.or_des_ln(float(x)) for x in xs])
+    want = np.log(xs.astype(np.float64))
+    err = np.abs(ln - want) / np.maximum(np.abs(want), 1e-30)
+    assert np.max(err[np.abs(want) > 1e-3]) < 5e-7
+    assert np.max(np.abs(ln - want)) < 1e-7 * 84
+    assert lib.or_des_ln(1.0) == 0.0
+    ys = np.concatenate([r.uniform(-20, 20, 4000), [0.0, -0.3466, 0.3466]]).astype(np.float32)
+    ex = np.array([lib.or_des_exp(float(y)) for y in ys])
+    assert np.max(np.abs(ex / np.exp(ys.astype(np.float64)) - 1.0)) < 5e-7
+    assert lib.or_des_exp(0.0) == 1.0
+    us = np.concatenate([r.uniform(0, 1, 4000), np.arange(9) / 8.0]).astype(np.float32)
+    co = np.array([lib.or_des_cos2pi(float(u)) for u in us])
+    assert np.max(np.abs(co - np.cos(2 * np.pi * us.astype(np.float64)))) < 2e-7
+    assert lib.or_des_cos2pi(0.0) == 1.0 and lib.or_des_cos2pi(0.5) == -1.0
