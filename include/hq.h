@@ -385,8 +385,11 @@ void hq_mlp_destroy(hq_mlp* m);
  *   window length), resp (reps: summed travel time of the calls served in the window).
  *   mem: HQ_HOST or HQ_DEVICE for every array; stream as for hq_create.  Utilisation is
  *   busy / window, the mean response time resp / sum(served).  Blocks until done.
- *   Errors: HQ_EINVAL (sizes, kind, NULL, a bad pref row, negative or non-finite rates),
- *   HQ_ECUDA. */
+ *   The variates are formed in FP32, so the rates have a range: nu_i and the total rate
+ *   sum_j lambda_j must lie in [2^-60, 2^60] (every service and inter-arrival time is
+ *   then a finite FP32 number).
+ *   Errors: HQ_EINVAL (sizes, kind, NULL, a bad pref row, negative or non-finite rates,
+ *   rates out of that range), HQ_ECUDA. */
 int hq_des_simulate(int N, int J, const double* lambda_j, const double* nu, const int32_t* pref,
                     const double* travel, int service_kind, int64_t reps, int64_t arrivals,
                     int64_t warmup, uint64_t seed, double* busy, int64_t* served, int64_t* lost,

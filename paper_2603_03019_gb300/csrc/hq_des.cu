@@ -26,6 +26,16 @@
 // from their series, every step one explicit round-to-nearest operation; the clock and
 // the sums are FP64.  On this GPU the FP32 pipe is many times faster than the FP64 one,
 // and the same steps in the CPU oracle give every replication the same trajectory.
+//
+// What remains FP64 in the loop is kept off the FP64 pipe where an exact integer form
+// exists: the node search compares the node's 53-bit draw with per-node integer
+// thresholds (K_j = the largest k with RN(k 2^-53 lambda) <= cdf_j, so "cdf_j >= the
+// target" is "K_j >= k"); the free-unit scan compares the bit patterns of non-negative
+// finite doubles, which order as integers; the unit's mean 1/nu_i and its derived
+// constants are a per-unit table.  The part of a service time that does not depend on
+// the unit is drawn at the top of the loop with the next inter-arrival time and node
+// (three independent chains the scheduler interleaves) and finished once the unit is
+// known; a lost call's draw is wasted.  Each replication's trajectory is unchanged.
 #include "hq_internal.cuh"
 
 namespace {
@@ -40,9 +50,10 @@ __device__ __forceinline__ uint64_t des_mix(uint64_t z) {
   return z ^ (z >> 31);
 }
 
-__device__ __forceinline__ double des_u53(uint64_t key, uint64_t c) {
+// the node's uniform is k 2^-53 with k = (x >> 11) + 1 in 1..2^53; the search uses k itself
+__device__ __forceinline__ uint64_t des_k53(uint64_t key, uint64_t c) {
   const uint64_t x = des_mix(key + (c + 1) * kGamma);
-  return __dmul_rn((double)((x >> 11) + 1), 0x1.0p-53);
+  return (x >> 11) + 1;
 }
 
 __device__ __forceinline__ float des_u24(uint64_t key, uint64_t c) {
@@ -131,40 +142,81 @@ __device__ __forceinline__ float des_normal(float u1, float u2) {
   return __fmul_rn(__fsqrt_rn(__fmul_rn(-2.0f, des_ln(u1))), des_cos2pi(u2));
 }
 
-__device__ float des_service(int kind, float m, uint64_t key, uint64_t c0) {
-  const float u2 = des_u24(key, c0), u3 = des_u24(key, c0 + 1);
+// The log-normal's variance parameter: ln 2, the exponential's variance for a unit mean
+constexpr float kLnS2 = 0x1.62e43p-1f;
+
+// The unit-independent part g of a service time from draws c0.. (Section 5.5's shapes):
+// exponential ln u; log-normal a standard normal; gamma of shape 5 ln(u u' u'' u');
+// gamma of shape 1/2 Z^2; uniform u.
+template <int kKind>
+__device__ __forceinline__ float des_shape(uint64_t key, uint64_t c0) {
+  const float u2 = des_u24(key, c0);
+  if (kKind == 0) return des_ln(u2);
+  if (kKind == 4) return u2;
+  const float u3 = des_u24(key, c0 + 1);
+  if (kKind == 1) return des_normal(u2, u3);
+  if (kKind == 3) {
+    const float z = des_normal(u2, u3);
+    return __fmul_rn(z, z);
+  }
+  float prod = __fmul_rn(u2, u3);
+  prod = __fmul_rn(prod, des_u24(key, c0 + 2));
+  prod = __fmul_rn(prod, des_u24(key, c0 + 3));
+  prod = __fmul_rn(prod, des_u24(key, c0 + 4));
+  return des_ln(prod);
+}
+
+// The per-unit constant pu of a service time of mean m: m for the exponential and the
+// gamma of shape 1/2, ln m - s^2/2 for the log-normal, m/5 for the gamma of shape 5, 2m
+// for the uniform.
+__device__ __forceinline__ float des_unit_const(int kind, float m) {
   switch (kind) {
-    case 0:
-      return __fmul_rn(-m, des_ln(u2));
-    case 1: {
-      const float s2 = 0x1.62e43p-1f;  // ln 2: the exponential's variance
-      const float mu = __fsub_rn(des_ln(m), __fmul_rn(0.5f, s2));
-      return des_exp(__fadd_rn(mu, __fmul_rn(__fsqrt_rn(s2), des_normal(u2, u3))));
-    }
-    case 2: {
-      float prod = __fmul_rn(u2, u3);
-      prod = __fmul_rn(prod, des_u24(key, c0 + 2));
-      prod = __fmul_rn(prod, des_u24(key, c0 + 3));
-      prod = __fmul_rn(prod, des_u24(key, c0 + 4));
-      return __fmul_rn(-__fdiv_rn(m, 5.0f), des_ln(prod));
-    }
-    case 3: {
-      const float z = des_normal(u2, u3);
-      return __fmul_rn(m, __fmul_rn(z, z));
-    }
+    case 1:
+      return __fsub_rn(des_ln(m), __fmul_rn(0.5f, kLnS2));
+    case 2:
+      return __fdiv_rn(m, 5.0f);
+    case 4:
+      return __fmul_rn(2.0f, m);
     default:
-      return __fmul_rn(__fmul_rn(2.0f, m), u2);
+      return m;
   }
 }
 
-// cumulative node rates, summed in node order by one thread (the oracle's order)
-__global__ void k_des_cdf(int J, const double* lam_j, double* cdf) {
+// the service time from its per-unit constant and its shape part
+template <int kKind>
+__device__ __forceinline__ float des_finish(float pu, float g) {
+  if (kKind == 0 || kKind == 2) return __fmul_rn(-pu, g);
+  if (kKind == 1) return des_exp(__fadd_rn(pu, __fmul_rn(__fsqrt_rn(kLnS2), g)));
+  return __fmul_rn(pu, g);
+}
+
+// cumulative node rates, summed in node order by one thread (the oracle's order); bit 2
+// of the flag if the total rate is outside [2^-60, 2^60]
+__global__ void k_des_cdf(int J, const double* lam_j, double* cdf, int* flag) {
   if (blockIdx.x != 0 || threadIdx.x != 0) return;
   double acc = 0.0;
   for (int j = 0; j < J; j++) {
     acc = __dadd_rn(acc, lam_j[j]);
     cdf[j] = acc;
   }
+  if (!(acc >= 0x1.0p-60 && acc <= 0x1.0p+60)) atomicOr(flag, 4);
+}
+
+// Per node the integer threshold K_j = max{k in 0..2^53 : RN(RN(k 2^-53) lambda) <= cdf_j}
+// (a binary search: the product is non-decreasing in k); per unit the service constant.
+__global__ void k_des_prep(int N, int J, int kind, const double* cdf, const double* nu, uint64_t* kth,
+                           float* pu) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < N) pu[j] = des_unit_const(kind, __double2float_rn(__ddiv_rn(1.0, nu[j])));
+  if (j >= J) return;
+  const double lam = cdf[J - 1], cj = cdf[j];
+  uint64_t lo = 0, hi = 1ull << 53;
+  while (lo < hi) {
+    const uint64_t mid = hi - ((hi - lo) >> 1);
+    if (__dmul_rn(__dmul_rn((double)mid, 0x1.0p-53), lam) <= cj) lo = mid;
+    else hi = mid - 1;
+  }
+  kth[j] = lo;
 }
 
 struct DesArgs {
@@ -172,7 +224,8 @@ struct DesArgs {
   int64_t reps, arrivals, warmup;
   uint64_t seed;
   const double* cdf;
-  const double* nu;
+  const uint64_t* kth;  // J node thresholds
+  const float* pu;      // N per-unit service constants
   const int32_t* pref;
   const double* travel;
   double* busy;     // reps x N
@@ -182,12 +235,12 @@ struct DesArgs {
   double* resp;     // reps
 };
 
+template <int kKind>
 __global__ void __launch_bounds__(kDesThreads) k_des_loss(DesArgs a) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= a.reps) return;
   const int N = a.N, J = a.J;
-  const double lam = __ldg(a.cdf + J - 1);
-  const float lamf = __double2float_rn(lam);
+  const float lamf = __double2float_rn(__ldg(a.cdf + J - 1));
   const uint64_t key = des_mix(a.seed + (uint64_t)(r + 1) * kGamma);
   double fr[kDesMaxN], busy[kDesMaxN];
   int64_t served[kDesMaxN];
@@ -200,25 +253,30 @@ __global__ void __launch_bounds__(kDesThreads) k_des_loss(DesArgs a) {
   double resp = 0.0, t = 0.0, t0 = 0.0;
   for (int64_t k = 0; k < a.arrivals; k++) {
     const uint64_t c = 8 * (uint64_t)k;
-    t = __dadd_rn(t, (double)__fdiv_rn(-des_ln(des_u24(key, c)), lamf));
+    // three independent chains: inter-arrival time, node draw, the service time's shape
+    const float dt = __fdiv_rn(-des_ln(des_u24(key, c)), lamf);
+    const uint64_t kn = des_k53(key, c + 1);
+    const float g = des_shape<kKind>(key, c + 2);
+    t = __dadd_rn(t, (double)dt);
     const bool in_window = k >= a.warmup;
     if (k == a.warmup) {
       t0 = t;
       for (int i = 0; i < N; i++)
         if (fr[i] > t0) busy[i] = __dsub_rn(fr[i], t0);
     }
-    const double target = __dmul_rn(des_u53(key, c + 1), lam);
     int lo = 0, hi = J - 1;
     while (lo < hi) {
       const int mid = (lo + hi) / 2;
-      if (__ldg(a.cdf + mid) >= target) hi = mid;
+      if (__ldg(a.kth + mid) >= kn) hi = mid;
       else lo = mid + 1;
     }
     const int j = lo;
+    // fr and t are finite and >= +0, so their bit patterns order as integers
+    const long long tb = __double_as_longlong(t);
     int unit = -1;
     for (int h = 0; h < N; h++) {
       const int i = __ldg(a.pref + (int64_t)j * N + h);
-      if (fr[i] <= t) {
+      if (__double_as_longlong(fr[i]) <= tb) {
         unit = i;
         break;
       }
@@ -227,7 +285,7 @@ __global__ void __launch_bounds__(kDesThreads) k_des_loss(DesArgs a) {
       if (in_window) lost++;
       continue;
     }
-    const double s = (double)des_service(a.kind, __double2float_rn(__ddiv_rn(1.0, __ldg(a.nu + unit))), key, c + 2);
+    const double s = (double)des_finish<kKind>(__ldg(a.pu + unit), g);
     fr[unit] = __dadd_rn(t, s);
     if (in_window) {
       busy[unit] = __dadd_rn(busy[unit], s);
@@ -249,7 +307,7 @@ __global__ void k_des_check(int N, int J, const double* lam_j, const double* nu,
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j < N) {
     const double v = nu[j];
-    if (!(v > 0.0) || isinf(v)) atomicOr(flag, 2);
+    if (!(v >= 0x1.0p-60 && v <= 0x1.0p+60)) atomicOr(flag, 2);
   }
   if (j >= J) return;
   const double l = lam_j[j];
@@ -305,7 +363,8 @@ extern "C" int hq_des_simulate(int N, int J, const double* lambda_j, const doubl
   int64_t *d_served = served, *d_lost = lost;
   const size_t in_bytes = 8 * nJ + 8 * nN + 4 * nJN + 8 * nJN + 16;
   const size_t out_bytes = 8 * nR * nN + 8 * nR * nN + 8 * nR * 3 + 64;
-  HQ_CUDA(cudaMalloc(&b_cdf.p, 8 * nJ + 16));
+  // cumulative rates (J), node thresholds (J), unit constants (32 floats), the flag
+  HQ_CUDA(cudaMalloc(&b_cdf.p, 16 * nJ + 4 * kDesMaxN + 16));
   if (mem == HQ_HOST) {
     HQ_CUDA(cudaMalloc(&b_in.p, in_bytes));
     HQ_CUDA(cudaMalloc(&b_out.p, out_bytes));
@@ -336,10 +395,15 @@ extern "C" int hq_des_simulate(int N, int J, const double* lambda_j, const doubl
     o += 8 * nR;
     d_resp = (double*)o;
   }
-  int* d_flag = (int*)((double*)b_cdf.p + nJ);
+  double* d_cdf = (double*)b_cdf.p;
+  uint64_t* d_kth = (uint64_t*)(d_cdf + nJ);
+  float* d_pu = (float*)(d_kth + nJ);
+  int* d_flag = (int*)(d_pu + kDesMaxN);
   HQ_CUDA(cudaMemsetAsync(d_flag, 0, sizeof(int), st));
   const int chk = J > N ? J : N;
   k_des_check<<<(chk + 127) / 128, 128, 0, st>>>(N, J, d_lam, d_nu, d_pref, d_flag);
+  HQ_LAUNCHED();
+  k_des_cdf<<<1, 32, 0, st>>>(J, d_lam, d_cdf, d_flag);
   HQ_LAUNCHED();
   int host_flag = 0;
   HQ_CUDA(cudaMemcpyAsync(&host_flag, d_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -348,11 +412,12 @@ extern "C" int hq_des_simulate(int N, int J, const double* lambda_j, const doubl
     hq_set_error("hq_des_simulate: a preference row is not a permutation of 0..N-1");
     return HQ_EINVAL;
   }
-  if (host_flag & 2) {
-    hq_set_error("hq_des_simulate: lambda_j must be finite and >= 0, nu finite and > 0");
+  if (host_flag & 6) {
+    hq_set_error("hq_des_simulate: lambda_j must be finite and >= 0 with a total in [2^-60, 2^60], "
+                 "nu in [2^-60, 2^60]");
     return HQ_EINVAL;
   }
-  k_des_cdf<<<1, 32, 0, st>>>(J, d_lam, (double*)b_cdf.p);
+  k_des_prep<<<(chk + 127) / 128, 128, 0, st>>>(N, J, service_kind, d_cdf, d_nu, d_kth, d_pu);
   HQ_LAUNCHED();
   DesArgs a;
   a.N = N;
@@ -362,8 +427,9 @@ extern "C" int hq_des_simulate(int N, int J, const double* lambda_j, const doubl
   a.arrivals = arrivals;
   a.warmup = warmup;
   a.seed = seed;
-  a.cdf = (const double*)b_cdf.p;
-  a.nu = d_nu;
+  a.cdf = d_cdf;
+  a.kth = d_kth;
+  a.pu = d_pu;
   a.pref = d_pref;
   a.travel = d_travel;
   a.busy = d_busy;
@@ -371,7 +437,23 @@ extern "C" int hq_des_simulate(int N, int J, const double* lambda_j, const doubl
   a.lost = d_lost;
   a.window = d_window;
   a.resp = d_resp;
-  k_des_loss<<<(unsigned)((reps + kDesThreads - 1) / kDesThreads), kDesThreads, 0, st>>>(a);
+  const unsigned grid = (unsigned)((reps + kDesThreads - 1) / kDesThreads);
+  switch (service_kind) {
+    case 0:
+      k_des_loss<0><<<grid, kDesThreads, 0, st>>>(a);
+      break;
+    case 1:
+      k_des_loss<1><<<grid, kDesThreads, 0, st>>>(a);
+      break;
+    case 2:
+      k_des_loss<2><<<grid, kDesThreads, 0, st>>>(a);
+      break;
+    case 3:
+      k_des_loss<3><<<grid, kDesThreads, 0, st>>>(a);
+      break;
+    default:
+      k_des_loss<4><<<grid, kDesThreads, 0, st>>>(a);
+  }
   HQ_LAUNCHED();
   if (mem == HQ_HOST) {
     HQ_CUDA(cudaMemcpyAsync(busy, d_busy, 8 * nR * nN, cudaMemcpyDeviceToHost, st));

@@ -95,3 +95,10 @@ def test_errors(gpu_lib):
             hq.hq_des_simulate(inst.N, inst.J, inst.lam_j, inst.nu, args[0], tt, args[1], args[2], args[3],
                                args[4], 1)
         assert ex.value.code == hq.HQ_EINVAL
+    # rates outside [2^-60, 2^60]: a unit's and the total
+    tiny_nu = inst.nu.copy()
+    tiny_nu[1] = 2.0 ** -61
+    for lam, nu in ((inst.lam_j, tiny_nu), (inst.lam_j * 2.0 ** -70, inst.nu)):
+        with pytest.raises(hq.HQError) as ex:
+            hq.hq_des_simulate(inst.N, inst.J, lam, nu, inst.pref, tt, 1, 10, 1000, 10, 1)
+        assert ex.value.code == hq.HQ_EINVAL
