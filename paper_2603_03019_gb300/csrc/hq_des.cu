@@ -30,7 +30,9 @@
 // What remains FP64 in the loop is kept off the FP64 pipe where an exact integer form
 // exists: the node search compares the node's 53-bit draw with per-node integer
 // thresholds (K_j = the largest k with RN(k 2^-53 lambda) <= cdf_j, so "cdf_j >= the
-// target" is "K_j >= k"); the free-unit scan compares the bit patterns of non-negative
+// target" is "K_j >= k"), starting from a guide table (Chen and Asau's method: the
+// first node of each of 1024 equal ranges of k); FP32 values widen to FP64 by moving
+// their bits; the free-unit scan compares the bit patterns of non-negative
 // finite doubles, which order as integers; the unit's mean 1/nu_i and its derived
 // constants are a per-unit table.  The part of a service time that does not depend on
 // the unit is drawn at the top of the loop with the next inter-arrival time and node
@@ -42,6 +44,7 @@ namespace {
 
 constexpr int kDesMaxN = 32;
 constexpr int kDesThreads = 64;
+constexpr int kGuideBits = 10;  // the guide table: 2^10 ranges of the 53-bit node draw
 constexpr uint64_t kGamma = 0x9e3779b97f4a7c15ULL;
 
 __device__ __forceinline__ uint64_t des_mix(uint64_t z) {
@@ -59,6 +62,22 @@ __device__ __forceinline__ uint64_t des_k53(uint64_t key, uint64_t c) {
 __device__ __forceinline__ float des_u24(uint64_t key, uint64_t c) {
   const uint64_t x = des_mix(key + (c + 1) * kGamma);
   return __fmul_rn((float)((x >> 40) + 1), 0x1.0p-24f);
+}
+
+// the FP64 value of an FP32 x (exact), by moving its bits: sign, exponent rebased from
+// 127 to 1023, fraction shifted to the top; a subnormal x is normalised first
+__device__ __forceinline__ double des_widen(float x) {
+  const uint32_t b = __float_as_uint(x);
+  const uint64_t sign = (uint64_t)(b >> 31) << 63;
+  int e = (int)((b >> 23) & 0xffu);
+  uint32_t m = b & 0x7fffffu;
+  if (e == 0) {
+    if (m == 0) return __longlong_as_double((long long)sign);
+    const int sh = __clz(m) - 8;
+    m = (m << sh) & 0x7fffffu;
+    e = 1 - sh;
+  }
+  return __longlong_as_double((long long)(sign | ((uint64_t)(e + 896) << 52) | ((uint64_t)m << 29)));
 }
 
 // a * b + c with two roundings (never contracted into one FMA)
@@ -219,12 +238,28 @@ __global__ void k_des_prep(int N, int J, int kind, const double* cdf, const doub
   kth[j] = lo;
 }
 
+// guide[b] = the first node j with K_j >= b 2^(53 - kGuideBits) + 1, the smallest draw of
+// range b (K_{J-1} = 2^53, so it exists)
+__global__ void k_des_guide(int J, const uint64_t* kth, int32_t* guide) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= (1 << kGuideBits)) return;
+  const uint64_t kmin = ((uint64_t)b << (53 - kGuideBits)) + 1;
+  int lo = 0, hi = J - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi) / 2;
+    if (kth[mid] >= kmin) hi = mid;
+    else lo = mid + 1;
+  }
+  guide[b] = lo;
+}
+
 struct DesArgs {
   int N, J, kind;
   int64_t reps, arrivals, warmup;
   uint64_t seed;
   const double* cdf;
   const uint64_t* kth;  // J node thresholds
+  const int32_t* guide; // 2^kGuideBits starting nodes
   const float* pu;      // N per-unit service constants
   const int32_t* pref;
   const double* travel;
@@ -257,20 +292,16 @@ __global__ void __launch_bounds__(kDesThreads) k_des_loss(DesArgs a) {
     const float dt = __fdiv_rn(-des_ln(des_u24(key, c)), lamf);
     const uint64_t kn = des_k53(key, c + 1);
     const float g = des_shape<kKind>(key, c + 2);
-    t = __dadd_rn(t, (double)dt);
+    t = __dadd_rn(t, des_widen(dt));
     const bool in_window = k >= a.warmup;
     if (k == a.warmup) {
       t0 = t;
       for (int i = 0; i < N; i++)
         if (fr[i] > t0) busy[i] = __dsub_rn(fr[i], t0);
     }
-    int lo = 0, hi = J - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi) / 2;
-      if (__ldg(a.kth + mid) >= kn) hi = mid;
-      else lo = mid + 1;
-    }
-    const int j = lo;
+    // the first node with K_j >= kn, from its range's first candidate (K_{J-1} = 2^53)
+    int j = __ldg(a.guide + ((kn - 1) >> (53 - kGuideBits)));
+    while (j < J - 1 && __ldg(a.kth + j) < kn) j++;
     // fr and t are finite and >= +0, so their bit patterns order as integers
     const long long tb = __double_as_longlong(t);
     int unit = -1;
@@ -285,7 +316,7 @@ __global__ void __launch_bounds__(kDesThreads) k_des_loss(DesArgs a) {
       if (in_window) lost++;
       continue;
     }
-    const double s = (double)des_finish<kKind>(__ldg(a.pu + unit), g);
+    const double s = des_widen(des_finish<kKind>(__ldg(a.pu + unit), g));
     fr[unit] = __dadd_rn(t, s);
     if (in_window) {
       busy[unit] = __dadd_rn(busy[unit], s);
@@ -363,8 +394,9 @@ extern "C" int hq_des_simulate(int N, int J, const double* lambda_j, const doubl
   int64_t *d_served = served, *d_lost = lost;
   const size_t in_bytes = 8 * nJ + 8 * nN + 4 * nJN + 8 * nJN + 16;
   const size_t out_bytes = 8 * nR * nN + 8 * nR * nN + 8 * nR * 3 + 64;
-  // cumulative rates (J), node thresholds (J), unit constants (32 floats), the flag
-  HQ_CUDA(cudaMalloc(&b_cdf.p, 16 * nJ + 4 * kDesMaxN + 16));
+  // cumulative rates (J), node thresholds (J), unit constants (32 floats), guide table,
+  // the flag
+  HQ_CUDA(cudaMalloc(&b_cdf.p, 16 * nJ + 4 * kDesMaxN + 4 * (1 << kGuideBits) + 16));
   if (mem == HQ_HOST) {
     HQ_CUDA(cudaMalloc(&b_in.p, in_bytes));
     HQ_CUDA(cudaMalloc(&b_out.p, out_bytes));
@@ -398,7 +430,8 @@ extern "C" int hq_des_simulate(int N, int J, const double* lambda_j, const doubl
   double* d_cdf = (double*)b_cdf.p;
   uint64_t* d_kth = (uint64_t*)(d_cdf + nJ);
   float* d_pu = (float*)(d_kth + nJ);
-  int* d_flag = (int*)(d_pu + kDesMaxN);
+  int32_t* d_guide = (int32_t*)(d_pu + kDesMaxN);
+  int* d_flag = (int*)(d_guide + (1 << kGuideBits));
   HQ_CUDA(cudaMemsetAsync(d_flag, 0, sizeof(int), st));
   const int chk = J > N ? J : N;
   k_des_check<<<(chk + 127) / 128, 128, 0, st>>>(N, J, d_lam, d_nu, d_pref, d_flag);
@@ -419,6 +452,8 @@ extern "C" int hq_des_simulate(int N, int J, const double* lambda_j, const doubl
   }
   k_des_prep<<<(chk + 127) / 128, 128, 0, st>>>(N, J, service_kind, d_cdf, d_nu, d_kth, d_pu);
   HQ_LAUNCHED();
+  k_des_guide<<<(1 << kGuideBits) / 128, 128, 0, st>>>(J, d_kth, d_guide);
+  HQ_LAUNCHED();
   DesArgs a;
   a.N = N;
   a.J = J;
@@ -430,6 +465,7 @@ extern "C" int hq_des_simulate(int N, int J, const double* lambda_j, const doubl
   a.cdf = d_cdf;
   a.kth = d_kth;
   a.pu = d_pu;
+  a.guide = d_guide;
   a.pref = d_pref;
   a.travel = d_travel;
   a.busy = d_busy;
