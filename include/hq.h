@@ -258,8 +258,7 @@ double hq_sweep_bytes(const hq_solver* h, int precision);
  *      layout as hq_get_table;
  *   stream: a cudaStream_t or NULL.
  * Calls no cudaMalloc/cudaFree.  The first call on each device looks up the static
- * array's device address (with that device current); make that first call before
- * any stream capture.  All calls share the array: calls that overlap on the GPU
+ * array's device address (with that device current).  All calls share the array: calls that overlap on the GPU
  * race and must be ordered (same stream, or synchronise in between).  Returns after
  * the work has finished on `stream`; on HQ_EINVAL from a bad row the contents of T
  * are unspecified. */
