@@ -740,7 +740,8 @@ def run_des(args):
     MPRE.  Per case 38,912 replications (256 per SM) of 1,000 calls, the first 200 not
     counted: 3.1e7 counted calls, more than the paper's 20 replications of 10^6, spread
     over enough independent replications to fill the GPU (each replication is one
-    thread's sequential event loop).  Beside it the oracle's simulation on one host
+    thread's sequential event loop).  The rate is taken through the public call with host
+    arrays (copies and set-up included).  Beside it the oracle's simulation on one host
     core, timed on a bounded sample."""
     import torch
 
@@ -787,7 +788,7 @@ def run_des(args):
     line = {"metric": "Section 5.5 check: MPRE of MRT and utilisation, GPU simulation vs hypercube "
                       "solution (15 cases per service distribution)",
             "value": calls / gpu_s, "unit": "simulated calls/s", "n_gpus": 1, "higher_is_better": True,
-            "data": "synthetic", "dtype": "f64",
+            "data": "synthetic", "dtype": "f32 variates, f64 clock",
             "config": {"workload": "des_n8_12_j71_loads0.1-0.9", "replications": reps, "calls": arr,
                        "warmup_calls": warm, "cases": len(cases)},
             "mpre": rows, "gpu_seconds": gpu_s,
