@@ -141,3 +141,17 @@ def test_series_functions_are_accurate():
     co = np.array([lib.or_des_cos2pi(float(u)) for u in us])
     assert np.max(np.abs(co - np.cos(2 * np.pi * us.astype(np.float64)))) < 2e-7
     assert lib.or_des_cos2pi(0.0) == 1.0 and lib.or_des_cos2pi(0.5) == -1.0
+
+
+def test_summary_pools_ratios_of_sums_by_hand():
+    """Two replications worked by hand: utilisation is total busy / total window (not
+    the mean of the per-replication ratios), the mean response time total travel /
+    total served, the loss probability total lost / total counted; the standard errors
+    come from the per-replication ratios (two values a, b: |a - b| / 2)."""
+    e = oracle.des_summary(busy=[[1.0, 2.0], [3.0, 4.0]], served=[[1, 1], [2, 0]], lost=[1, 3],
+                           window=[10.0, 30.0], resp=[5.0, 9.0], counted=10)
+    assert e["util"] == pytest.approx([0.1, 0.15], abs=1e-15)
+    assert e["mrt"] == pytest.approx(3.5, abs=1e-15)
+    assert e["p_lost"] == pytest.approx(0.2, abs=1e-15)
+    assert e["util_se"] == pytest.approx([0.0, (0.2 - 4.0 / 30.0) / 2], abs=1e-15)
+    assert e["mrt_se"] == pytest.approx(1.0, abs=1e-15)
