@@ -53,6 +53,26 @@ def test_device_inputs_and_ragged_sizes(gpu_lib):
     assert np.allclose(g1["busy"], r1["busy"], rtol=1e-11)
 
 
+def test_largest_n_and_more_nodes_than_guide_ranges(gpu_lib):
+    """N = 32 (the largest the simulation takes) and J = 3,000 nodes, more than the
+    1,024 ranges of the node search's guide table, so several nodes share a range and
+    the search walks past its first candidate; some nodes have zero demand.  Counts
+    equal to the oracle's, times to rounding."""
+    inst = I.des_instance(3232, N=32, load=0.8, J=3000)
+    lam = inst.lam_j.copy()
+    lam[::7] = 0.0
+    lam *= inst.lam_j.sum() / lam.sum()
+    tt = I.travel_times(inst)
+    for kind in ("lognormal", "gamma5"):
+        g = hq.hq_des_simulate(inst.N, inst.J, lam, inst.nu, inst.pref, tt, kind, 33, 4000, 300, 8)
+        r = oracle.des_loss(N=inst.N, J=inst.J, mode=oracle.LOSS, C=0, lam_j=lam, nu=inst.nu, pref=inst.pref,
+                            travel=tt, kind=kind, reps=33, arrivals=4000, warmup=300, seed=8)
+        assert np.array_equal(g["served"], r["served"])
+        assert np.array_equal(g["lost"], r["lost"])
+        for k in ("busy", "window", "resp"):
+            assert np.allclose(g[k], r[k], rtol=1e-11, atol=0), (kind, k)
+
+
 @pytest.mark.parametrize("kind", KINDS)
 def test_against_the_gpu_solution(gpu_lib, kind):
     """N = 12, load 0.7: 2,048 replications of 20,000 calls against the hypercube
