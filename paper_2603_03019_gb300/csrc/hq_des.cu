@@ -165,8 +165,8 @@ __device__ __forceinline__ float des_normal(float u1, float u2) {
 constexpr float kLnS2 = 0x1.62e43p-1f;
 
 // The unit-independent part g of a service time from draws c0.. (Section 5.5's shapes):
-// exponential ln u; log-normal a standard normal; gamma of shape 5 ln(u u' u'' u');
-// gamma of shape 1/2 Z^2; uniform u.
+// exponential ln u; log-normal a standard normal; gamma of shape 5 ln of the product of
+// five uniforms; gamma of shape 1/2 Z^2; uniform u.
 template <int kKind>
 __device__ __forceinline__ float des_shape(uint64_t key, uint64_t c0) {
   const float u2 = des_u24(key, c0);
