@@ -122,7 +122,7 @@ def run_profile(args):
     torch.cuda.synchronize()
     if args.precision == "ir":
         # correction sweeps: a short FP32 solve, then one launch of `sweeps` correction
-        # sweeps against an FP64 base of its result (the second k_persist launch)
+        # sweeps against an FP64 base of its result (the second k_sweep launch)
         rc, st = s.solve(tol=0.0, tol_kind=hq.HQ_TOL_STEP, precision="fp32", max_sweeps=4,
                          check_every=4, order=args.order)
         hq.hq_profile_sweep(s.h, hq.HQ_PREC_FP32_IR, args.sweeps)
