@@ -133,16 +133,50 @@ def _check(rc: int, allow=(HQ_OK,)) -> int:
     return rc
 
 
-def _ptr(a):
-    """(address, mem) of a numpy array or torch tensor."""
+def _ptr(a, dtype, count: int, name: str):
+    """(address, mem) of a numpy array or torch tensor (None: (None, HOST)), after the
+    checks the C side cannot make on a bare pointer: the element type (`dtype`, or one of
+    a tuple of types of the same width), C-contiguity, at least `count` elements, and for
+    a CUDA tensor the current device (the kernels run there)."""
     if a is None:
         return None, HQ_HOST
+    wants = [np.dtype(d) for d in (dtype if isinstance(dtype, tuple) else (dtype,))]
     if isinstance(a, np.ndarray):
-        assert a.flags["C_CONTIGUOUS"]
+        if a.dtype not in wants or not a.flags["C_CONTIGUOUS"]:
+            raise ValueError(f"{name}: a C-contiguous {wants[0]} array is needed")
+        if a.size < count:
+            raise ValueError(f"{name}: {a.size} elements, {count} needed")
         return a.ctypes.data, HQ_HOST
-    # torch tensor
-    assert a.is_contiguous()
+    import torch
+
+    if a.dtype not in [_TORCH_DTYPES[w.str] for w in wants] or not a.is_contiguous():
+        raise ValueError(f"{name}: a contiguous {wants[0]} tensor is needed")
+    if a.numel() < count:
+        raise ValueError(f"{name}: {a.numel()} elements, {count} needed")
+    if a.is_cuda and a.device.index != torch.cuda.current_device():
+        raise ValueError(f"{name}: on {a.device}, not on the current device")
     return a.data_ptr(), (HQ_DEVICE if a.is_cuda else HQ_HOST)
+
+
+class _TorchDtypes(dict):
+    """numpy dtype string -> torch dtype, filled on first use (torch imported lazily)."""
+
+    def __missing__(self, key):
+        import torch
+
+        self.update({"<f8": torch.float64, "<f4": torch.float32, "<i4": torch.int32,
+                     "<u4": torch.uint32 if hasattr(torch, "uint32") else torch.int32,
+                     "<i8": torch.int64})
+        return dict.__getitem__(self, key)
+
+
+_TORCH_DTYPES = _TorchDtypes()
+
+
+def _sizes(h: int) -> tuple[int, int, int, int]:
+    """(N, J, mode, C) of a solver."""
+    info = hq_get_info(h)
+    return int(info[0]), int(info[1]), int(info[2]), int(info[3])
 
 
 # ---- the C calls, same names ------------------------------------------------------------
@@ -161,9 +195,10 @@ def hq_create(N: int, J: int, mode: int = HQ_LOSS, capacity_C: int = 0, stream=N
 
 
 def hq_load(h: int, lambda_j, nu, pref) -> None:
-    pl, ml = _ptr(lambda_j)
-    pn, mn = _ptr(nu)
-    pp, mp = _ptr(pref)
+    N, J, _, _ = _sizes(h)
+    pl, ml = _ptr(lambda_j, np.float64, J, "lambda_j")
+    pn, mn = _ptr(nu, np.float64, N, "nu")
+    pp, mp = _ptr(pref, np.int32, J * N, "pref")
     if not (ml == mn == mp):
         raise ValueError("lambda_j, nu and pref must live in the same memory")
     _check(load().hq_load(h, pl, pn, pp, ml))
@@ -177,37 +212,45 @@ def hq_solve(h: int, opts: hq_opts | None = None, allow_notconverged: bool = Tru
     return rc, st
 
 
-def _get(fn, h, out, *extra):
-    p, m = _ptr(out)
-    _check(getattr(load(), fn)(h, p, *extra, m))
+def _get(fn, h, out, count):
+    p, m = _ptr(out, np.float64, count, fn)
+    _check(getattr(load(), fn)(h, p, m))
     return out
 
 
 def hq_get_stationary(h, out):
-    return _get("hq_get_stationary", h, out)
+    N, _, _, _ = _sizes(h)
+    return _get("hq_get_stationary", h, out, 1 << N)
 
 
 def hq_get_conditional(h, out):
-    return _get("hq_get_conditional", h, out)
+    N, _, _, _ = _sizes(h)
+    return _get("hq_get_conditional", h, out, 1 << N)
 
 
 def hq_get_layer_marginals(h, out, tail=None):
-    p, m = _ptr(out)
-    pt, mt = _ptr(tail)
+    N, _, mode, C = _sizes(h)
+    p, m = _ptr(out, np.float64, N + 1 + (C if mode == HQ_FINITE else 0), "p_n")
+    pt, mt = _ptr(tail, np.float64, 1, "tail")
+    if tail is not None and mt != m:
+        raise ValueError("p_n and tail must live in the same memory")
     _check(load().hq_get_layer_marginals(h, p, pt, m))
     return out
 
 
 def hq_get_utilisation(h, out):
-    return _get("hq_get_utilisation", h, out)
+    N, _, _, _ = _sizes(h)
+    return _get("hq_get_utilisation", h, out, N)
 
 
 def hq_get_response_pattern(h, out):
-    return _get("hq_get_response_pattern", h, out)
+    N, J, _, _ = _sizes(h)
+    return _get("hq_get_response_pattern", h, out, J * N)
 
 
 def hq_get_workload(h, out):
-    return _get("hq_get_workload", h, out)
+    N, J, _, _ = _sizes(h)
+    return _get("hq_get_workload", h, out, N * J)
 
 
 def hq_get_summary(h) -> np.ndarray:
@@ -217,8 +260,11 @@ def hq_get_summary(h) -> np.ndarray:
 
 
 def hq_get_table(h, T=None, masks=None):
-    pt, mt = _ptr(T)
-    pm, mm = _ptr(masks)
+    info = hq_get_info(h)
+    pt, mt = _ptr(T, np.float64, int(info[5]), "T")
+    pm, mm = _ptr(masks, (np.uint32, np.int32), int(info[4]), "masks")
+    if T is not None and masks is not None and mt != mm:
+        raise ValueError("T and masks must live in the same memory")
     _check(load().hq_get_table(h, pt, pm, mt if T is not None else mm))
     return T, masks
 
@@ -327,49 +373,68 @@ def hq_mlp_num_params(m: int) -> int:
 
 
 def hq_mlp_set_weights(m: int, w) -> None:
-    p, mem = _ptr(w)
+    p, mem = _ptr(w, np.float32, hq_mlp_num_params(m), "w")
     _check(load().hq_mlp_set_weights(m, p, hq_mlp_num_params(m), mem))
 
 
 def hq_mlp_get_weights(m: int, out=None):
     if out is None:
         out = np.empty(hq_mlp_num_params(m), dtype=np.float32)
-    p, mem = _ptr(out)
+    p, mem = _ptr(out, np.float32, hq_mlp_num_params(m), "w")
     _check(load().hq_mlp_get_weights(m, p, hq_mlp_num_params(m), mem))
     return out
 
 
+def _device_rows(X, target, name: str) -> tuple[int, int, int]:
+    """(B, X address, target address) of B rows of 9 network inputs and B targets, both
+    float32 CUDA tensors on the current device."""
+    B = int(X.shape[0])
+    px, mx = _ptr(X, np.float32, 9 * B, "X")
+    pt, mt = _ptr(target, np.float32, B, name)
+    if mx != HQ_DEVICE or mt != HQ_DEVICE:
+        raise ValueError(f"X and {name} must be CUDA tensors")
+    return B, px, pt
+
+
 def hq_mlp_forward(m: int, X, y) -> None:
-    """X: (B, 8) float32 CUDA tensor; y: (B,) float32 CUDA tensor."""
-    _check(load().hq_mlp_forward(m, X.data_ptr(), X.shape[0], y.data_ptr()))
+    """X: (B, 9) float32 CUDA tensor; y: (B,) float32 CUDA tensor."""
+    B, px, py = _device_rows(X, y, "y")
+    _check(load().hq_mlp_forward(m, px, B, py))
 
 
 def hq_mlp_gradients(m: int, X, target, grad=None) -> float:
     loss = ctypes.c_float(0.0)
-    _check(load().hq_mlp_gradients(m, X.data_ptr(), target.data_ptr(), X.shape[0],
-                                   grad.data_ptr() if grad is not None else None,
-                                   ctypes.addressof(loss)))
+    B, px, pt = _device_rows(X, target, "target")
+    pg, mg = _ptr(grad, np.float32, hq_mlp_num_params(m), "grad")
+    if grad is not None and mg != HQ_DEVICE:
+        raise ValueError("grad must be a CUDA tensor")
+    _check(load().hq_mlp_gradients(m, px, pt, B, pg, ctypes.addressof(loss)))
     return float(loss.value)
 
 
 def hq_mlp_train_step(m: int, X, target, lr: float, want_loss: bool = True):
     loss = ctypes.c_float(0.0)
-    _check(load().hq_mlp_train_step(m, X.data_ptr(), target.data_ptr(), X.shape[0], lr,
-                                    ctypes.addressof(loss) if want_loss else None))
+    B, px, pt = _device_rows(X, target, "target")
+    _check(load().hq_mlp_train_step(m, px, pt, B, lr, ctypes.addressof(loss) if want_loss else None))
     return float(loss.value) if want_loss else None
 
 
 def hq_mlp_features(h: int, out=None, N: int | None = None):
     """Network inputs, one row per (layer n = 1..N-1, unit i): (N (N-1), 9) float32."""
+    n = _sizes(h)[0]
+    if N is not None and N != n:
+        raise ValueError(f"hq_mlp_features: the solver has N = {n}, not {N}")
     if out is None:
-        out = np.empty((N * (N - 1), 9), dtype=np.float32)
-    p, mem = _ptr(out)
+        out = np.empty((n * (n - 1), 9), dtype=np.float32)
+    p, mem = _ptr(out, np.float32, 9 * n * (n - 1), "X")
     _check(load().hq_mlp_features(h, p, mem))
     return out
 
 
 def hq_mlp_predict(h: int, m: int, N: int) -> tuple[np.ndarray, np.ndarray, np.ndarray]:
     """(q (N+1, N), layer law P(n), rho) of the model for the loaded instance."""
+    if N != _sizes(h)[0]:
+        raise ValueError(f"hq_mlp_predict: the solver has N = {_sizes(h)[0]}, not {N}")
     q = np.empty((N + 1, N))
     pn = np.empty(N + 1)
     rho = np.empty(N)
@@ -442,9 +507,9 @@ class Solver:
         o.omega = omega
         keep = None
         if warm_p is not None:
-            p, m = _ptr(np.ascontiguousarray(warm_p, dtype=np.float64)
-                        if isinstance(warm_p, np.ndarray) else warm_p)
-            keep = warm_p
+            # keep the buffer handed to C (a converted copy, for a numpy input) alive
+            keep = np.ascontiguousarray(warm_p, dtype=np.float64) if isinstance(warm_p, np.ndarray) else warm_p
+            p, m = _ptr(keep, np.float64, 1 << self.N, "warm_p")
             o.warm_start = HQ_WARM_GIVEN
             o.warm_p = p
             o.warm_mem = m
@@ -538,13 +603,17 @@ def hq_des_simulate(N: int, J: int, lam_j, nu, pref, travel, kind, reps: int, ar
                    lost=torch.empty(reps, dtype=torch.int64, device=dev),
                    window=torch.empty(reps, dtype=torch.float64, device=dev),
                    resp=torch.empty(reps, dtype=torch.float64, device=dev))
-        for a, dt in ((lam_j, torch.float64), (nu, torch.float64), (pref, torch.int32), (travel, torch.float64)):
-            if a.dtype != dt or not a.is_cuda or not a.is_contiguous():
-                raise ValueError("hq_des_simulate: device inputs must be contiguous CUDA tensors "
-                                 "(float64 rates and travel times, int32 preferences)")
         mem = HQ_DEVICE
-    pa = [_ptr(x)[0] for x in (lam_j, nu, pref, travel)]
-    po = [_ptr(out[k2])[0] for k2 in ("busy", "served", "lost", "window", "resp")]
+    pa = []
+    for x, dt, n, name in ((lam_j, np.float64, J, "lambda_j"), (nu, np.float64, N, "nu"),
+                           (pref, np.int32, J * N, "pref"), (travel, np.float64, J * N, "travel")):
+        p, m = _ptr(x, dt, n, name)
+        if m != mem:
+            raise ValueError("hq_des_simulate: all inputs in host memory, or all CUDA tensors")
+        pa.append(p)
+    po = [_ptr(out[k2], dt, n, k2)[0]
+          for k2, dt, n in (("busy", np.float64, reps * N), ("served", np.int64, reps * N),
+                            ("lost", np.int64, reps), ("window", np.float64, reps), ("resp", np.float64, reps))]
     sp = stream.cuda_stream if stream is not None and hasattr(stream, "cuda_stream") else stream
     _check(load().hq_des_simulate(N, J, *pa, k, reps, arrivals, warmup, ctypes.c_uint64(seed), *po, mem, sp))
     return out
