@@ -137,9 +137,11 @@ typedef struct hq_stats {
 
 typedef struct hq_solver hq_solver;
 
-/* Fill opts with defaults: tol 1e-10 on the residual, FP32 then DF64 sweeps (valid
+/* Fill opts with defaults (library configuration, no counterpart in the paper; the
+ * paper leaves epsilon open): tol 1e-10 on the residual, FP32 then DF64 sweeps (valid
  * for single and batched solves; HQ_PREC_FP32_IR is faster for single solves), check
- * every 8 sweeps, max 100000 sweeps, omega 1, cold start. */
+ * every 8 sweeps, max 100000 sweeps, omega 1 (Algorithm 1 unrelaxed), the uniform
+ * start of Algorithm 1. */
 void hq_default_opts(hq_opts* opts);
 
 /* The model of Section 2.1 (N units with their own service rates, J demand nodes with
@@ -184,7 +186,8 @@ int hq_get_stationary(hq_solver* h, double* P, int mem);
  * HQ_INFINITE, queue[0] receives sum_{c>=1} P~{c} if queue != NULL. */
 int hq_get_layer_marginals(hq_solver* h, double* pn, double* queue_tail, int mem);
 
-/* Conditional probabilities p_n(B) (each layer sums to 1), y-order, 2^N values. */
+/* Conditional probabilities p_n(B) of Proposition 1 (the iterate of Algorithm 1; each
+ * layer sums to 1, Lemma 1), y-order, 2^N values, host or device memory per mem. */
 int hq_get_conditional(hq_solver* h, double* p, int mem);
 
 /* rho_i: fraction of time unit i is busy (queued states count as busy), N values:
@@ -219,8 +222,9 @@ int hq_get_summary(hq_solver* h, double* out5);
  * Also writes the layer-ranked state masks (2^N uint32) if masks != NULL. */
 int hq_get_table(hq_solver* h, double* T, uint32_t* masks, int mem);
 
-/* Sizes of the solver: out[0]=N, [1]=J, [2]=mode, [3]=C, [4]=2^N,
- * [5]=table entries, [6]=device bytes allocated.  8 int64 slots, host memory. */
+/* Sizes of the solver (library bookkeeping, not in the paper): out[0]=N, [1]=J,
+ * [2]=mode, [3]=C, [4]=2^N, [5]=table entries (N 2^(N-1), the pull entries of Eq. 3),
+ * [6]=device bytes allocated.  8 int64 slots, host memory. */
 int hq_get_info(const hq_solver* h, int64_t* out8);
 
 /* Timing of the hot path: run `sweeps` outer iterations (Algorithm 1) of the current
@@ -232,9 +236,9 @@ int hq_get_info(const hq_solver* h, int64_t* out8);
  * iterations; call hq_solve again for results.  Needs a previous hq_solve. */
 int hq_profile_sweep(hq_solver* h, int precision, int sweeps, float* ms_out);
 
-/* Phase timing of the last launch of the sweep kernel (for profiling): the kernel
- * runs one phase per layer per sweep plus a closing phase, separated by grid
- * barriers.  us_out (host, max_out doubles) receives the wall time of each phase in
+/* Phase timing of the last launch of the sweep kernel (for profiling; not in the
+ * paper): the kernel runs one phase per layer of Algorithm 1 per sweep plus a closing
+ * phase, separated by grid barriers.  us_out (host, max_out doubles) receives the wall time of each phase in
  * microseconds, measured on the GPU's global timer; returns the number of phases
  * written (at most 64 are recorded), or a negative hq_status. */
 int hq_profile_phases(hq_solver* h, double* us_out, int max_out);
@@ -403,7 +407,7 @@ const char* hq_strerror(int code);
 const char* hq_last_error(void);
 
 /* Device kernel launches made by the calling thread since the last reset (for
- * accounting of the work the library does). */
+ * accounting of the work the library does; not in the paper). */
 int64_t hq_launch_count(int reset);
 
 #ifdef __cplusplus
