@@ -38,12 +38,14 @@
 // rank blocks (the states of one layer sharing their high part, see HQ_SW_HI_BITS) are
 // sorted by cost and dealt to the warps of the grid in snake order, which evens out the
 // warps' totals; a block's items (runs of at most 32 consecutive states) go to one warp,
-// one lane per state.  Per block, the warp reads its neighbour block bases from RH once
-// (lane j: the block across high unit j; lanes 29..31: its own block and the blocks
-// (hi, w -/+ 1)), lists its high-part neighbour runs in shared memory, and copies the two
-// blocks that hold its states' low-part neighbours -- (hi, w-1) of layer n-1 and (hi, w+1)
-// of layer n+1, at most 252 states each -- into its shared-memory slot with 16-byte
-// asynchronous copies.  Per item, every lane issues all its loads at once before it
+// one lane per state.  A warp fetches the metadata of its next 32 blocks at once, one
+// lane per block (first item, descriptor, and the block's rank-table entries into a
+// per-warp shared buffer).  Per block, the warp takes its neighbour block bases from
+// that buffer (lane j: the block across high unit j; lanes 29..31: its own block and the
+// blocks (hi, w -/+ 1)), lists its high-part neighbour runs in shared memory, and
+// copies the two blocks that hold its states' low-part neighbours -- (hi, w-1) of layer
+// n-1 and (hi, w+1) of layer n+1, at most 252 states each -- into its shared-memory slot
+// with 16-byte asynchronous copies.  Per item, every lane issues all its loads at once before it
 // waits: its table record, its high-part neighbours (consecutive states have them at
 // consecutive ranks, so these are coalesced runs), r_m, its old value and its two weights.
 // Low-part neighbour positions and idle units come from a shared table per low part, so
@@ -73,7 +75,7 @@ namespace {
 
 using namespace hqdev;
 
-constexpr int kMaxPL = HQ_MAXN / 2;        // layers in one phase, at most (red-black, N = 28)
+constexpr int kMaxPL = HQ_MAXN / 2;        // layers in one phase, at most (red-black, N <= 29)
 constexpr int kMaxWords = 4 * kMaxPL + 1;  // partial words per CTA per phase
 constexpr unsigned kSpinDefault = 1u << 24;
 constexpr unsigned kFull = 0xffffffffu;
