@@ -10,6 +10,12 @@ Two independent routes:
   * ``oracle.dense.dense_solve`` -- a dense direct solve of the global balance
     equations (1)-(2) built straight from Eq. (3) in numpy (N <= 12).
 
+Also ``des_loss``: the discrete-event simulation of the loss system with general service
+times (Section 5.5) in plain C (``des.c``).  Its sample path is defined with FP32
+variates from series functions and an FP64 clock (the paper gives its simulation no
+precision), the one place the oracle computes in FP32; it is pinned to Erlang-B, the
+exact solution and the samplers' moments.
+
 Arguments are plain arrays: N, J, lam_j (J,), nu (N,), pref (J, N) int32 with
 pref[j, h] = zeta_j(h+1) (0-based unit ids), mode 0 loss / 1 finite / 2 infinite,
 C the buffer size (finite mode).  Any object with those attributes can be passed
